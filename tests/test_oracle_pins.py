@@ -1,0 +1,554 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix,
+independently of the oracle's own code:
+
+- Maxwell-Boltzmann moments by Gauss-Hermite quadrature (Eqs. MBmoments27, Peq,
+  Qeq, PMB, QMB, anomalya);
+- energy moments by symbolic differentiation with sympy (Eqs. Operator, Ecompact,
+  geqmom) and, for a monatomic gas, by quadrature of the MB energy distribution
+  (Eq. MBE);
+- textbook D3Q27 / D2Q9 weights and isotropy at T = 1/3 (Sec. II.C);
+- conservation (Eqs. density, momentum, energy);
+- hydrodynamic limit (Sec. II.E, Eqs. mu, bulkvisc, kappa, Pr, gamma): sound speed,
+  sound attenuation at rest and under advection (Galilean invariance, the purpose of
+  the correction, Sec. II.C), shear-wave decay, thermal diffusivity, power-law mu;
+- exact Riemann solution (Sod, Sec. III.B) and normal-shock relations (Sec. III.C);
+- exact reduction D3Q27 -> D2Q9 for z-uniform flow.
+
+Every test is marked "not gpu" implicitly (no marker) and runs on the CPU.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+import pytest
+import sympy as sp
+
+import oracle as O
+from paper_2102_09512_gb300 import cases as C
+import exact_riemann as R
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def read_golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+def params_of(c: C.Case, **kw) -> O.Params:
+    d = dict(D=c.D, nx=c.nx, ny=c.ny, nz=c.nz, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0,
+             mu_exp=c.mu_exp, bc=c.bc)
+    d.update(kw)
+    return O.Params(**d)
+
+
+# --------------------------------------------------------------------------
+# quadrature of the Maxwellian: E[h(c)] with c ~ N(u, T I)
+# --------------------------------------------------------------------------
+_X, _W = np.polynomial.hermite_e.hermegauss(12)
+_W = _W / math.sqrt(2.0 * math.pi)
+
+
+def mb_moment(D, rho, u, T, h):
+    """rho (2 pi T)^{-D/2} int h(c) exp(-(c-u)^2 / 2T) dc, exact for polynomials of
+    degree <= 23 per axis."""
+    s = 0.0
+    st = math.sqrt(T)
+    if D == 2:
+        for a, wa in zip(_X, _W):
+            for b, wb in zip(_X, _W):
+                s += wa * wb * h(u[0] + st * a, u[1] + st * b, 0.0)
+    else:
+        for a, wa in zip(_X, _W):
+            for b, wb in zip(_X, _W):
+                for k, wk in zip(_X, _W):
+                    s += wa * wb * wk * h(u[0] + st * a, u[1] + st * b, u[2] + st * k)
+    return rho * s
+
+
+def lattice_moment(cvec, pops, l, m, n):
+    return float(np.sum(cvec[:, 0] ** l * cvec[:, 1] ** m * cvec[:, 2] ** n * pops))
+
+
+RNG = np.random.default_rng(12345)
+STATES = [(1.0 + 0.3 * RNG.random(), RNG.uniform(-0.3, 0.3, 3), RNG.uniform(0.08, 0.4)) for _ in range(4)]
+
+
+# --------------------------------------------------------------------------
+# lattice and weights
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("D", [2, 3])
+def test_velocity_set(D):
+    c = O.velocities(D)
+    Q = 3 ** D
+    assert c.shape == (Q, 3)
+    assert len({tuple(v) for v in c}) == Q
+    assert set(c[:, :D].ravel()) == {-1, 0, 1}
+    assert np.all(c[:, D:] == 0)
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_rest_weights_and_isotropy(D):
+    """At u = 0, T = 1/3 the product form gives the textbook weights
+    (D3Q27: 8/27, 2/27, 1/54, 1/216; D2Q9: 4/9, 1/9, 1/36) and fourth-order
+    isotropy, which fails at any other T (sum w c_x^4 = T vs 3 T^2)."""
+    p = O.Params(D=D)
+    c = O.velocities(D)
+    w = O.feq(p, 1.0, [0, 0, 0], 1.0 / 3.0)
+    c2 = np.sum(c * c, axis=1)
+    expect = {2: {0: 4 / 9, 1: 1 / 9, 2: 1 / 36}, 3: {0: 8 / 27, 1: 2 / 27, 2: 1 / 54, 3: 1 / 216}}[D]
+    for k, v in expect.items():
+        assert np.allclose(w[c2 == k], v, rtol=0, atol=1e-15)
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert abs(lattice_moment(c, w, 4, 0, 0) - 3 * (1 / 3) ** 2) < 1e-15
+    assert abs(lattice_moment(c, w, 2, 2, 0) - (1 / 3) ** 2) < 1e-15
+    w2 = O.feq(p, 1.0, [0, 0, 0], 0.2)
+    assert abs(lattice_moment(c, w2, 4, 0, 0) - 3 * 0.2 ** 2) > 1e-2
+
+
+# --------------------------------------------------------------------------
+# f-equilibria
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("D", [2, 3])
+@pytest.mark.parametrize("k", range(len(STATES)))
+def test_feq_matches_maxwell_boltzmann_moments(D, k):
+    """sum c_x^l c_y^m c_z^n f^eq = F^MB_lmn for l,m,n in {0,1,2} (Eq. MBmoments27)."""
+    rho, u, T = STATES[k]
+    u = u.copy()
+    if D == 2:
+        u[2] = 0
+    p = O.Params(D=D)
+    c = O.velocities(D)
+    f = O.feq(p, rho, u, T)
+    for l in range(3):
+        for m in range(3):
+            for n in range(3 if D == 3 else 1):
+                ref = mb_moment(D, rho, u, T, lambda x, y, z: x ** l * y ** m * z ** n)
+                assert lattice_moment(c, f, l, m, n) == pytest.approx(ref, rel=1e-13, abs=1e-14)
+
+
+@pytest.mark.parametrize("k", range(len(STATES)))
+def test_anomaly_is_only_diagonal_third_moment(k):
+    """Q^eq - Q^MB vanishes off the diagonal and equals rho u_a (1 - 3T) - rho u_a^3 on
+    it (Eqs. Qeq, QMB, Deviation)."""
+    rho, u, T = STATES[k]
+    p = O.Params(D=3)
+    c = O.velocities(3)
+    f = O.feq(p, rho, u, T)
+    for a in range(3):
+        for b in range(3):
+            for g in range(3):
+                e = [0, 0, 0]
+                for idx in (a, b, g):
+                    e[idx] += 1
+                lat = lattice_moment(c, f, *e)
+                mb = mb_moment(3, rho, u, T, lambda x, y, z: x ** e[0] * y ** e[1] * z ** e[2])
+                dev = lat - mb
+                if a == b == g:
+                    assert dev == pytest.approx(rho * u[a] * (1 - 3 * T) - rho * u[a] ** 3, rel=1e-12, abs=1e-14)
+                else:
+                    assert abs(dev) < 1e-14
+
+
+@pytest.mark.parametrize("k", range(len(STATES)))
+def test_fex_moments(k):
+    """f^ex keeps rho, rho u and the off-diagonal stresses, and shifts the diagonal
+    ones by (2-w)/(2w) d_a Q~ (Eq. Pstar)."""
+    rho, u, T = STATES[k]
+    p = O.Params(D=3)
+    c = O.velocities(3)
+    omega = 1.3
+    dQ = np.array([0.01, -0.02, 0.005])
+    f = O.fex(p, rho, u, T, omega, dQ)
+    feq = O.feq(p, rho, u, T)
+    assert lattice_moment(c, f, 0, 0, 0) == pytest.approx(rho, rel=1e-14)
+    for a in range(3):
+        e = [0, 0, 0]
+        e[a] = 1
+        assert lattice_moment(c, f, *e) == pytest.approx(rho * u[a], rel=1e-13, abs=1e-15)
+        e[a] = 2
+        shift = lattice_moment(c, f, *e) - lattice_moment(c, feq, *e)
+        assert shift == pytest.approx((2 - omega) / (2 * omega) * dQ[a], rel=1e-11)
+    assert lattice_moment(c, f, 1, 1, 0) == pytest.approx(rho * u[0] * u[1], rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# g-equilibria: symbolic operator moments (sympy) and MB energy moments
+# --------------------------------------------------------------------------
+def sympy_energy_moments(D, gamma):
+    ux, uy, uz, T, rho = sp.symbols("ux uy uz T rho")
+    us = (ux, uy, uz)
+    Cv = 1 / (sp.Rational(gamma).limit_denominator(1000) - 1)
+    E = Cv * T + (ux ** 2 + uy ** 2 + (uz ** 2 if D == 3 else 0)) / 2
+
+    def Op(A, v):
+        return sp.expand(T * sp.diff(A, v) + v * A)
+
+    G = {}
+    for l in range(3):
+        A = E
+        for _ in range(l):
+            A = Op(A, ux)
+        for m in range(3):
+            B = A
+            for _ in range(m):
+                B = Op(B, uy)
+            for n in range(3 if D == 3 else 1):
+                Cc = B
+                for _ in range(n):
+                    Cc = Op(Cc, uz)
+                G[(l, m, n)] = sp.lambdify((rho, ux, uy, uz, T), rho * Cc, "math")
+    return G
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_geq_matches_operator_moments(D):
+    """sum c^l c^m c^n g^eq = rho O_x^l O_y^m O_z^n E for l,m,n <= 2 (Eqs. geqmom,
+    Ecompact); the 27 (9) moments determine the populations."""
+    gamma = 1.4
+    G = sympy_energy_moments(D, gamma)
+    p = O.Params(D=D, gamma=gamma)
+    c = O.velocities(D)
+    for rho, u, T in STATES:
+        u = u.copy()
+        if D == 2:
+            u[2] = 0
+        g = O.geq(p, rho, u, T)
+        for (l, m, n), fn in G.items():
+            ref = fn(rho, u[0], u[1], u[2], T)
+            assert lattice_moment(c, g, l, m, n) == pytest.approx(ref, rel=1e-12, abs=1e-14)
+
+
+@pytest.mark.parametrize("k", range(len(STATES)))
+def test_geq_monatomic_is_maxwell_boltzmann(k):
+    """For Cv = 3/2 (gamma = 5/3) the generating function is E^MB (Eq. Etr), so the
+    g^eq moments equal the MB energy moments G^MB_lmn (Eqs. MBE, MBEcompact)."""
+    rho, u, T = STATES[k]
+    p = O.Params(D=3, gamma=5.0 / 3.0)
+    c = O.velocities(3)
+    g = O.geq(p, rho, u, T)
+    for l in range(3):
+        for m in range(3):
+            for n in range(3):
+                ref = mb_moment(3, rho, u, T,
+                                lambda x, y, z: x ** l * y ** m * z ** n * 0.5 * (x * x + y * y + z * z))
+                assert lattice_moment(c, g, l, m, n) == pytest.approx(ref, rel=1e-12, abs=1e-14)
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_qeq_and_Req_closed_forms(D):
+    """q^eq = (H + u^2/2) rho u and R^eq = (H + u^2/2) P^eq + P u u with H = Cp T
+    (Eqs. qeq, Req)."""
+    gamma = 1.4
+    Cp = gamma / (gamma - 1.0)
+    p = O.Params(D=D, gamma=gamma)
+    c = O.velocities(D)
+    for rho, u, T in STATES:
+        u = u.copy()
+        if D == 2:
+            u[2] = 0
+        g = O.geq(p, rho, u, T)
+        h = Cp * T + 0.5 * float(u @ u)
+        for a in range(D):
+            e = [0, 0, 0]
+            e[a] = 1
+            assert lattice_moment(c, g, *e) == pytest.approx(h * rho * u[a], rel=1e-12)
+        for a in range(D):
+            for b in range(D):
+                e = [0, 0, 0]
+                e[a] += 1
+                e[b] += 1
+                Peq = rho * T * (a == b) + rho * u[a] * u[b]
+                ref = h * Peq + rho * T * u[a] * u[b]
+                assert lattice_moment(c, g, *e) == pytest.approx(ref, rel=1e-12, abs=1e-15)
+
+
+def _perturbed_populations(p, rho, u, T, seed):
+    rng = np.random.default_rng(seed)
+    f = O.feq(p, rho, u, T) * (1 + 0.05 * rng.standard_normal(p.Q))
+    g = O.geq(p, rho, u, T) * (1 + 0.05 * rng.standard_normal(p.Q))
+    return f, g
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_gstar_changes_only_the_energy_flux(D):
+    """g* has the moments of g^eq except the first ones (Eq. gqeqmom)."""
+    p = O.Params(D=D, mu0=0.01)
+    c = O.velocities(D)
+    for k, (rho, u, T) in enumerate(STATES):
+        u = u.copy()
+        if D == 2:
+            u[2] = 0
+        f, g = _perturbed_populations(p, rho, u, T, k)
+        out = O.collide_node(p, f, g, [0.003, -0.001, 0.002])
+        for l in range(3):
+            for m in range(3):
+                for n in range(3 if D == 3 else 1):
+                    if l + m + n == 1:
+                        continue
+                    a = lattice_moment(c, out["gstar"], l, m, n)
+                    b = lattice_moment(c, out["geq"], l, m, n)
+                    assert a == pytest.approx(b, rel=1e-12, abs=1e-15)
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_collision_conserves_per_node(D):
+    """Collision conserves rho, rho u, rho E at every node (Eqs. density, momentum, energy)."""
+    p = O.Params(D=D, mu0=0.004, Pr=0.7)
+    c = O.velocities(D)
+    for k, (rho, u, T) in enumerate(STATES):
+        u = u.copy()
+        if D == 2:
+            u[2] = 0
+        f, g = _perturbed_populations(p, rho, u, T, 100 + k)
+        out = O.collide_node(p, f, g, [0.01, 0.02, -0.01])
+        assert out["f_post"].sum() == pytest.approx(f.sum(), rel=1e-15)
+        assert out["g_post"].sum() == pytest.approx(g.sum(), rel=1e-15)
+        for a in range(3):
+            assert float(c[:, a] @ out["f_post"]) == pytest.approx(float(c[:, a] @ f), rel=1e-14, abs=1e-15)
+
+
+def test_pr_one_reduces_g_to_plain_bgk():
+    """Pr = 1 gives omega_1 = omega (Eq. Pr), so the g update is plain BGK to g^eq."""
+    p = O.Params(D=3, mu0=0.01, Pr=1.0)
+    rho, u, T = STATES[0]
+    f, g = _perturbed_populations(p, rho, u, T, 7)
+    out = O.collide_node(p, f, g, [0.01, 0.0, -0.02])
+    # omega depends on the node's own rho and T, taken from the populations
+    cvec = O.velocities(3)
+    mrho = f.sum()
+    uu = (cvec.T @ f) / mrho
+    Tn = (g.sum() / mrho - 0.5 * uu @ uu) * 0.4
+    w, w1 = O.rates(p, mrho, Tn)
+    assert w1 == pytest.approx(w, rel=1e-15)
+    assert np.allclose(out["g_post"], g + w * (out["geq"] - g), rtol=1e-14, atol=1e-16)
+
+
+def test_rates_reproduce_mu_and_pr():
+    """omega and omega_1 reproduce mu = (1/w - 1/2) P and the Prandtl number (Eqs. mu, Pr)."""
+    p = O.Params(D=3, mu0=0.013, Pr=0.71, mu_exp=0.76, T0=0.15)
+    for rho, T in [(1.0, 0.15), (0.7, 0.2), (1.3, 0.09)]:
+        w, w1 = O.rates(p, rho, T)
+        mu = 0.013 * (T / 0.15) ** 0.76
+        assert (1 / w - 0.5) * rho * T == pytest.approx(mu, rel=1e-14)
+        assert w1 * (2 - w) / (w * (2 - w1)) == pytest.approx(0.71, rel=1e-14)
+
+
+# --------------------------------------------------------------------------
+# grid-level invariants
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("D,shape", [(2, (13, 7, 1)), (3, (6, 5, 4))])
+def test_global_conservation_periodic(D, shape):
+    nx, ny, nz = shape
+    c = C.random_smooth(D, nx, ny, nz, seed=3, mu0=0.02)
+    p = params_of(c)
+    s = O.init(p, c.rho, c.u, c.T)
+    c0 = O.conservation(s)
+    O.step(s, 60 if D == 2 else 20)
+    c1 = O.conservation(s)
+    scale = np.array([c0[0], c0[0], c0[0], c0[0], c0[4]])
+    assert np.all(np.abs(c1 - c0) / scale < 2e-14)
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_uniform_flow_is_a_fixed_point(D):
+    """A uniform state (with flow) initialised at equilibrium stays put: the
+    equilibria are Galilean-consistent and the derivative term vanishes."""
+    n = (5, 4, 3) if D == 3 else (7, 5, 1)
+    rho = np.full(n[::-1], 0.9)
+    T = np.full(n[::-1], 0.17)
+    u = np.zeros((D,) + n[::-1])
+    u[0] = 0.21
+    u[1] = -0.13
+    for bc in [(0,) * 6, (1, 1, 0, 0, 1, 1)]:
+        p = O.Params(D=D, nx=n[0], ny=n[1], nz=n[2], mu0=0.01, bc=bc)
+        s = O.init(p, rho, u, T)
+        O.step(s, 10)
+        r2, u2, T2 = O.fields(s)
+        assert np.allclose(r2, 0.9, rtol=0, atol=1e-14)
+        assert np.allclose(u2[0], 0.21, rtol=0, atol=1e-14)
+        assert np.allclose(T2, 0.17, rtol=0, atol=1e-14)
+
+
+def test_d2q9_is_z_marginal_of_d3q27():
+    """For z-uniform fields with u_z = 0 the D3Q27 populations summed over c_z evolve
+    exactly as D2Q9 (the product form factorises, Eq. mom27UniQuE)."""
+    nx, ny = 11, 6
+    c2 = C.random_smooth(2, nx, ny, 1, seed=9, mu0=0.02, du=0.1)
+    bc = (1, 1, 0, 0, 0, 0)
+    p2 = params_of(c2, bc=bc)
+    s2 = O.init(p2, c2.rho, c2.u, c2.T)
+    nz = 3
+    rho3 = np.repeat(c2.rho, nz, axis=0)
+    T3 = np.repeat(c2.T, nz, axis=0)
+    u3 = np.zeros((3, nz, ny, nx))
+    u3[0] = np.repeat(c2.u[0], nz, axis=0)
+    u3[1] = np.repeat(c2.u[1], nz, axis=0)
+    p3 = O.Params(D=3, nx=nx, ny=ny, nz=nz, mu0=0.02, bc=bc)
+    s3 = O.init(p3, rho3, u3, T3)
+    O.step(s2, 15)
+    O.step(s3, 15)
+    r2, v2, t2 = O.fields(s2)
+    r3, v3, t3 = O.fields(s3)
+    r3 = r3.reshape(nz, ny * nx)
+    t3 = t3.reshape(nz, ny * nx)
+    for z in range(nz):
+        assert np.max(np.abs(r3[z] - r2)) < 1e-13
+        assert np.max(np.abs(t3[z] - t2)) < 1e-13
+        for a in range(2):
+            assert np.max(np.abs(v3[a].reshape(nz, -1)[z] - v2[a])) < 1e-13
+    assert np.max(np.abs(v3[2])) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# hydrodynamic limit (Sec. II.E)
+# --------------------------------------------------------------------------
+def _mode(s, c, field_, k_axis_len):
+    rho, u, T = O.fields(s)
+    arr = {"rho": rho, "ux": u[0], "uy": u[1], "T": T}[field_].reshape(c.nz, c.ny, c.nx)[0, 0]
+    x = np.arange(k_axis_len)
+    k = 2 * math.pi / k_axis_len
+    return np.sum((arr - arr.mean()) * np.exp(-1j * k * x)) * 2 / k_axis_len
+
+
+def _track(c, p, field_, nsteps, every):
+    s = O.init(p, c.rho, c.u, c.T)
+    ts, amps = [0], [_mode(s, c, field_, c.nx)]
+    for n in range(every, nsteps + 1, every):
+        O.step(s, every)
+        ts.append(n)
+        amps.append(_mode(s, c, field_, c.nx))
+    return np.array(ts), np.array(amps)
+
+
+def _sound(U0, correction, D=2, T0=0.15, mu=0.01, L=64):
+    c = C.sound_wave(D=D, L=L, U0=U0, mu=mu, T0=T0, A=1e-5)
+    p = params_of(c, correction=correction)
+    ts, a = _track(c, p, "rho", 1500, 10)
+    sel = ts >= 200
+    Gam = -np.polyfit(ts[sel], np.log(np.abs(a[sel])), 1)[0]
+    freq = -np.polyfit(ts[sel], np.unwrap(np.angle(a))[sel], 1)[0]
+    k = 2 * math.pi / L
+    gamma, Pr = 1.4, c.Pr
+    Cv = 1.0 / (gamma - 1.0)
+    zeta = (2.0 / 3.0 - 1.0 / Cv) * mu            # Eq. bulkvisc
+    alpha = mu / Pr                                # kappa / (rho Cp), Eqs. kappa, Pr
+    Gam_nsf = 0.5 * k * k * ((4.0 / 3.0 * mu + zeta) + (gamma - 1.0) * alpha)
+    return freq / k - U0, math.sqrt(gamma * T0), Gam, Gam_nsf
+
+
+@pytest.mark.parametrize("U0", [0.0, 0.2])
+def test_sound_speed_and_attenuation(U0):
+    """A travelling acoustic wave moves at sqrt(gamma T) relative to the flow (Eq. gamma)
+    and decays at the NSF rate k^2/2 [(4/3 mu + varsigma)/rho + (gamma-1) kappa/(rho Cp)]
+    with the model's bulk viscosity (Eq. bulkvisc), at rest and advected."""
+    c_meas, c_exp, G, G_nsf = _sound(U0, 1)
+    assert c_meas == pytest.approx(c_exp, rel=2e-3)
+    assert G == pytest.approx(G_nsf, rel=0.02)
+
+
+def test_without_correction_attenuation_is_wrong():
+    """Planted mistake: dropping the extended-equilibrium correction (f^ex -> f^eq and
+    the div Q~ term of q*) spoils the normal stress, which the sound pin detects."""
+    _, _, G, G_nsf = _sound(0.2, 0)
+    assert abs(G / G_nsf - 1.0) > 0.5
+
+
+@pytest.mark.parametrize("mu_exp,T0", [(0.0, 0.15), (0.76, 0.2)])
+def test_shear_wave_viscosity(mu_exp, T0):
+    """A shear wave u_y = A sin(kx) decays at nu k^2, nu = mu/rho (Eq. mu), also when
+    advected along x; with the power law mu = mu0 (T/T0')^0.76 at T != T0'."""
+    L = 64
+    mu0 = 0.01
+    c = C.shear_wave(D=2, L=L, A=1e-5, U0=0.15, mu=mu0, T0=T0)
+    p = params_of(c, mu_exp=mu_exp, T0=0.15)
+    ts, a = _track(c, p, "uy", 1200, 20)
+    sel = ts >= 100
+    rate = -np.polyfit(ts[sel], np.log(np.abs(a[sel])), 1)[0]
+    mu = mu0 * (T0 / 0.15) ** mu_exp
+    k = 2 * math.pi / L
+    assert rate == pytest.approx(mu * k * k, rel=0.01)
+
+
+def test_thermal_diffusivity_gives_prandtl():
+    """An isobaric temperature wave decays at kappa k^2 / (rho Cp) with
+    kappa = (1/w1 - 1/2) Cp P (Eq. kappa), i.e. at mu k^2 / (rho Pr) (Eq. Pr)."""
+    L = 64
+    mu, Pr = 0.01, 0.5
+    c = C.thermal_wave(D=2, L=L, A=1e-5, mu=mu, Pr=Pr)
+    p = params_of(c)
+    ts, a = _track(c, p, "T", 2000, 20)
+    sel = ts >= 300
+    rate = -np.polyfit(ts[sel], np.log(np.abs(a[sel])), 1)[0]
+    k = 2 * math.pi / L
+    assert rate == pytest.approx(mu / Pr * k * k, rel=0.02)
+
+
+# --------------------------------------------------------------------------
+# shocks (Sec. III.B, III.C)
+# --------------------------------------------------------------------------
+def test_exact_riemann_solver_against_toro():
+    g = read_golden("sod_star_state_toro.txt")
+    ps, us, rl, rr = R.star_state(1.0, 0.0, 1.0, 0.125, 0.0, 0.1)
+    assert ps == pytest.approx(g["p_star"], abs=6e-6)
+    assert us == pytest.approx(g["u_star"], abs=6e-6)
+    assert rl == pytest.approx(g["rho_star_left"], abs=6e-6)
+    assert rr == pytest.approx(g["rho_star_right"], abs=6e-6)
+    ps2, us2, _, _ = R.star_state(1.0, 0.0, 0.15, 0.125, 0.0, 0.015)
+    assert ps2 == pytest.approx(0.15 * ps, rel=1e-12)
+    assert us2 == pytest.approx(math.sqrt(0.15) * us, rel=1e-12)
+
+
+def test_sod_against_exact_solution():
+    """Sod tube (Sec. III.B), 800 x 4 nodes, mu = 0.015, 500 steps: mean absolute
+    deviation from the exact inviscid solution.  Measured 2.1e-3 (rho) and 8.3e-4 (u);
+    the bounds keep a 2x margin."""
+    c = C.sod(nx=800, ny=4, mu=0.015)
+    p = params_of(c)
+    s = O.init(p, c.rho, c.u, c.T)
+    O.step(s, 500)
+    rho, u, T = O.fields(s)
+    rho = rho.reshape(4, 800)
+    ux = u[0].reshape(4, 800)
+    assert np.max(np.abs(rho - rho[0:1])) == 0.0
+    xi = (np.arange(800) + 0.5 - 400.0) / 500.0
+    re, ue, _ = R.sample(xi, 1.0, 0.0, 0.15, 0.125, 0.0, 0.015)
+    assert np.mean(np.abs(rho[0] - re)) < 4.5e-3
+    assert np.mean(np.abs(ux[0] - ue)) < 2.0e-3
+
+
+def test_standing_normal_shock_rankine_hugoniot():
+    """A Ma = 1.2 standing shock initialised with the Rankine-Hugoniot states (Sec. III.C)
+    stays in place and keeps the tabulated jump ratios."""
+    gold = read_golden("normal_shock_M1p2.txt")
+    r_rho, r_p, r_T, _ = C.rankine_hugoniot(1.2)
+    assert r_p == pytest.approx(gold["p2_over_p1"], abs=6e-5)
+    assert r_rho == pytest.approx(gold["rho2_over_rho1"], abs=6e-5)
+    assert r_T == pytest.approx(gold["T2_over_T1"], abs=6e-5)
+    nx, ny = 300, 2
+    c = C.shock_vortex(nx=nx, ny=ny, Ma_s=1.2, Ma_v=0.0, r_v=nx / 16.0, Re=150.0, Pr=0.75)
+    p = params_of(c)
+    s = O.init(p, c.rho, c.u, c.T)
+    O.step(s, 1500)
+    rho, u, T = O.fields(s)
+    rho = rho.reshape(ny, nx)[0]
+    T = T.reshape(ny, nx)[0]
+    P = rho * T
+    xs = c.extra["x_s"]
+    mid = 0.5 * (1.0 + r_rho)
+    pos = np.argmax(rho > mid)
+    assert abs(pos - xs) <= 2
+    up = slice(20, int(xs) - 30)
+    dn = slice(int(xs) + 30, nx - 20)
+    assert np.mean(rho[dn]) / np.mean(rho[up]) == pytest.approx(r_rho, rel=5e-3)
+    assert np.mean(P[dn]) / np.mean(P[up]) == pytest.approx(r_p, rel=5e-3)
+    assert np.mean(T[dn]) / np.mean(T[up]) == pytest.approx(r_T, rel=5e-3)
