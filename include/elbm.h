@@ -1,0 +1,160 @@
+/*
+ * elbm.h - C ABI of the GB300 (sm_103a) two-population compressible lattice
+ * Boltzmann library (Saadat, Hosseini, Dorschner & Karlin, arXiv:2102.09512).
+ *
+ * One time step updates both populations at every node (Eqs. fLBGK, gLBGK):
+ *   f_i(x + c_i, t + 1) = f_i + omega (f_i^ex - f_i)
+ *   g_i(x + c_i, t + 1) = g_i + omega_1 (g_i^eq - g_i) + (omega - omega_1)(g_i^eq - g_i^*)
+ * with the extended equilibrium f^ex (Eqs. extf, Pa_star), the operator
+ * product-form energy equilibrium g^eq (Eq. geq_i), the quasi-equilibrium g*
+ * (Eqs. gstar, qstar1), omega and omega_1 from mu and Pr (Eqs. mu, Pr), T from the
+ * total energy of an ideal gas with constant Cv = 1/(gamma - 1) (Eqs. U, E; R = 1),
+ * and the derivative of the anomaly Q~_aaa (Eq. anomalya) by first-order upwind
+ * differences (Sec. III.A).  Lattice units: dx = dt = 1.
+ *
+ * Conventions
+ *  - Node index n = x + nx*(y + ny*z).  Host and device field arrays are FP64:
+ *    rho[N], T[N], u[D*N] component-major (u_x block, then u_y, then u_z).
+ *  - Memory: the caller owns every device buffer (two population stores and one
+ *    auxiliary buffer, sizes from elbm_bytes_required) and the stream; the library
+ *    owns only the handle.  Population layout (structure of arrays): plane k of
+ *    N values for k = 0..2Q-1, f planes first, then g planes; direction
+ *    i = (c_x+1) + 3(c_y+1) + 9(c_z+1).  Device pointers must be 256-byte aligned.
+ *  - Calls are asynchronous on the bound stream unless stated; functions that
+ *    return host data synchronise the stream.
+ *  - Errors: every function returns an elbm_status (0 = ELBM_OK).  Argument errors
+ *    are reported synchronously.  Conditions found on the device (non-finite
+ *    moments, rho <= 0 or T <= 0) are latched in the auxiliary buffer and reported
+ *    by the next synchronising call as ELBM_ERR_NONPHYSICAL.
+ *  - A handle is not thread-safe.
+ */
+#ifndef ELBM_H
+#define ELBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ELBM_OK = 0,
+    ELBM_ERR_ARG = -1,          /* invalid argument or unbound handle            */
+    ELBM_ERR_UNSUPPORTED = -2,  /* valid but not implemented combination        */
+    ELBM_ERR_CUDA = -3,         /* a CUDA runtime call failed                     */
+    ELBM_ERR_NONPHYSICAL = -4,  /* device saw a non-finite value, rho<=0 or T<=0 */
+    ELBM_ERR_TIMEOUT = -5       /* a bounded device wait gave up                  */
+} elbm_status;
+
+typedef enum { ELBM_D2Q9 = 9, ELBM_D3Q27 = 27 } elbm_lattice;
+
+/* Per face -x,+x,-y,+y,-z,+z.  An axis is periodic on both faces or on neither.
+ * Zero-gradient: the ghost node holds a copy of the adjacent interior node (its
+ * post-collision populations and its Q~); the paper states no boundary type. */
+typedef enum { ELBM_BC_PERIODIC = 0, ELBM_BC_ZEROGRAD = 1 } elbm_bc;
+
+/* Population storage.  F64 and F32 store the populations; F16DEV and BF16DEV store
+ * their deviation from the rest state f^eq(rho_ref, 0, T_ref), g^eq(rho_ref, 0, T_ref)
+ * rounded to nearest even, with FP32 arithmetic. */
+typedef enum { ELBM_F64 = 0, ELBM_F32 = 1, ELBM_F16DEV = 2, ELBM_BF16DEV = 3 } elbm_store;
+
+/* Spatial derivative of Q~_aaa: first-order upwind (the paper's choice, Sec. III.A)
+ * or second-order central (its comparison variant). */
+typedef enum { ELBM_DERIV_UPWIND = 0, ELBM_DERIV_CENTRAL = 1 } elbm_deriv;
+
+/* Kernel schedule of one step. */
+typedef enum {
+    ELBM_KERNEL_FUSED = 0,    /* one kernel: halo-recomputed moments + collide + stream */
+    ELBM_KERNEL_TWOPASS = 1   /* moment/Q~ pass into the aux buffer, then collide+stream */
+} elbm_kernel;
+
+typedef struct {
+    int lattice;         /* ELBM_D2Q9 or ELBM_D3Q27                                  */
+    int nx, ny, nz;      /* grid; nz must be 1 for D2Q9                               */
+    double gamma;        /* adiabatic exponent (Eq. gamma), > 1                        */
+    double Pr;           /* Prandtl number (Eq. Pr), > 0                               */
+    double mu0;          /* dynamic viscosity at T0 (Eq. mu), > 0                      */
+    double T0;           /* reference temperature of the power law, > 0               */
+    double mu_exp;       /* mu = mu0 (T/T0)^mu_exp; 0 = constant (Sec. III.D uses 0.76) */
+    int bc[6];           /* elbm_bc per face                                          */
+    int store;           /* elbm_store                                                */
+    int deriv;           /* elbm_deriv                                                */
+    double rho_ref;      /* rest state of the deviation stores (ignored for F64/F32)  */
+    double T_ref;
+} elbm_params;
+
+typedef struct elbm_handle elbm_handle;
+
+/* Validates the parameters and creates a handle.  Host-only, no CUDA call. */
+int elbm_create(const elbm_params *params, elbm_handle **out);
+
+/* Bytes of each population store and of the auxiliary buffer (status word,
+ * reduction partials, the Q~ field of the two-pass schedule and a staging area
+ * for host field transfers). */
+int elbm_bytes_required(const elbm_handle *h, size_t *pop_bytes, size_t *aux_bytes);
+
+/* Binds caller-owned device buffers and a stream (cudaStream_t, may be NULL for
+ * the legacy default stream).  pop_a and pop_b are the two ping-pong stores; the
+ * state lives in pop_a after elbm_set_fields*.  Clears the status word. */
+int elbm_bind(elbm_handle *h, void *pop_a, void *pop_b, void *aux, void *stream);
+
+/* Initial state f = f^eq(rho,u,T), g = g^eq(rho,u,T) (no non-equilibrium part).
+ * _device: FP64 device arrays; plain: host arrays (copied through the aux staging
+ * area, synchronising). */
+int elbm_set_fields(elbm_handle *h, const double *rho, const double *u, const double *T);
+int elbm_set_fields_device(elbm_handle *h, const double *rho, const double *u, const double *T);
+
+/* Advances nsteps time steps with the selected kernel schedule (asynchronous). */
+int elbm_step(elbm_handle *h, int nsteps);
+
+/* rho, u, T of the current state (Eqs. density, momentum, energy, E).
+ * Plain: host arrays, synchronises and returns the latched device status.
+ * _device: FP64 device arrays, asynchronous. */
+int elbm_get_fields(elbm_handle *h, double *rho, double *u, double *T);
+int elbm_get_fields_device(elbm_handle *h, double *rho, double *u, double *T);
+
+/* Totals {sum rho, sum rho u_x, sum rho u_y, sum rho u_z, sum rho E} of the current
+ * state, FP64 with compensated summation (Eqs. density, momentum, energy).
+ * Synchronises. */
+int elbm_conservation(elbm_handle *h, double out[5]);
+
+/* The same totals of the state at the start of the last step, accumulated inside
+ * that step's kernel (fused schedule; FP32 per thread, FP64 compensated across
+ * threads).  Synchronises. */
+int elbm_step_totals(elbm_handle *h, double out[5]);
+
+/* Selects the kernel schedule (elbm_kernel).  Results agree to rounding. */
+int elbm_set_kernel(elbm_handle *h, int kernel);
+
+/* Length of the z segment each CTA of the fused D3Q27 kernel marches over
+ * (default min(nz, 32)); a tuning knob, results do not depend on it. */
+int elbm_set_tile_z(elbm_handle *h, int tz);
+
+/* Raw copy of the current population store (pop_bytes) to or from host memory,
+ * for checkpoint and restart.  Synchronises. */
+int elbm_get_populations(elbm_handle *h, void *host_dst);
+int elbm_set_populations(elbm_handle *h, const void *host_src);
+
+/* Synchronises the stream and returns the latched device status (and clears it). */
+int elbm_sync(elbm_handle *h);
+
+/* Number of time steps taken since the last elbm_set_fields*. */
+long long elbm_steps_done(const elbm_handle *h);
+
+/* Number of kernel launches this handle has issued (for launch accounting). */
+long long elbm_launch_count(const elbm_handle *h);
+
+/* Velocity c_i = (c[0], c[1], c[2]) of direction i of a lattice (Eq. d3q27vel). */
+int elbm_velocity(int lattice, int i, int c[3]);
+
+/* Frees the handle (not the caller's buffers). */
+int elbm_destroy(elbm_handle *h);
+
+/* Static string for a status code. */
+const char *elbm_status_str(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ELBM_H */

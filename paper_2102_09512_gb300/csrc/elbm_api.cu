@@ -1,0 +1,373 @@
+// C ABI of the library (declared in include/elbm.h): parameter validation, buffer
+// binding, schedule selection and the host side of the diagnostics.  No kernel here
+// touches the populations except the small reduction finaliser.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "elbm.h"
+#include "elbm_internal.h"
+
+using namespace elbm;
+
+struct elbm_handle {
+    elbm_params prm;
+    const Ops* ops;
+    KParams kp;
+    int D, Q;
+    long long N;
+    size_t pop_bytes;
+    AuxLayout aux;
+    void* pop[2];
+    char* auxp;
+    cudaStream_t stream;
+    bool bound;
+    int cur;                 // index of the store holding the current state
+    int kernel;              // elbm_kernel
+    int step_blocks;         // CTAs that wrote step partials in the last step
+    long long steps;
+    long long launches;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+const Ops* pick_ops(int D, int store) {
+    if (D == 2) {
+        switch (store) {
+            case ELBM_F64: return ops_d2_f64();
+            case ELBM_F32: return ops_d2_f32();
+            case ELBM_F16DEV: return ops_d2_f16();
+            case ELBM_BF16DEV: return ops_d2_bf16();
+        }
+    } else {
+        switch (store) {
+            case ELBM_F64: return ops_d3_f64();
+            case ELBM_F32: return ops_d3_f32();
+            case ELBM_F16DEV: return ops_d3_f16();
+            case ELBM_BF16DEV: return ops_d3_bf16();
+        }
+    }
+    return nullptr;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// Rest state f^eq(rho0, 0, T0), g^eq(rho0, 0, T0) of the deviation stores.  With
+// u = 0 the per-axis factors are phi = (T/2, 1-T, T/2) and psi = (T^2/2, -T^2, T^2/2).
+void rest_state(int D, double rho0, double T0, double gamma, float* out) {
+    const int Q = D == 3 ? 27 : 9;
+    const double Cv = 1.0 / (gamma - 1.0);
+    const double phi[3] = {0.5 * T0, 1.0 - T0, 0.5 * T0};
+    const double psi[3] = {0.5 * T0 * T0, -T0 * T0, 0.5 * T0 * T0};
+    for (int i = 0; i < Q; ++i) {
+        const int a = i % 3, b = (i / 3) % 3, c = D == 3 ? i / 9 : 1;
+        const double pz = D == 3 ? phi[c] : 1.0, sz = D == 3 ? psi[c] : 0.0;
+        const double f = rho0 * phi[a] * phi[b] * pz;
+        const double g = rho0 * ((Cv * T0 * phi[a] + psi[a]) * phi[b] * pz + phi[a] * (psi[b] * pz + phi[b] * sz));
+        out[i] = (float)f;
+        out[Q + i] = (float)g;
+    }
+}
+
+__global__ void finalize_kernel(const double* __restrict__ partials, int nb, double* __restrict__ out) {
+    double s[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0};
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {   // Neumaier
+            const double v = partials[5 * j + k];
+            const double t = s[k] + v;
+            c[k] += fabs(s[k]) >= fabs(v) ? (s[k] - t) + v : (v - t) + s[k];
+            s[k] = t;
+        }
+    }
+    __shared__ double red[5][256];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) red[k][threadIdx.x] = s[k] + c[k];
+    __syncthreads();
+    if (threadIdx.x < 5) {   // fixed-order compensated sum of the 256 thread values
+        const int k = threadIdx.x;
+        double ss = 0.0, cc = 0.0;
+        for (int j = 0; j < 256; ++j) {
+            const double v = red[k][j];
+            const double t = ss + v;
+            cc += fabs(ss) >= fabs(v) ? (ss - t) + v : (v - t) + ss;
+            ss = t;
+        }
+        out[k] = ss + cc;
+    }
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? ELBM_OK : ELBM_ERR_CUDA; }
+
+int* status_ptr(elbm_handle* h) { return (int*)(h->auxp + h->aux.status); }
+double* totals_ptr(elbm_handle* h) { return (double*)(h->auxp + h->aux.totals); }
+double* step_partials(elbm_handle* h) { return (double*)(h->auxp + h->aux.partials); }
+double* query_partials(elbm_handle* h) {
+    return (double*)(h->auxp + h->aux.partials) + 5 * (size_t)h->aux.max_blocks;
+}
+double* staging(elbm_handle* h) { return (double*)(h->auxp + h->aux.staging); }
+
+// Synchronise, read and clear the latched device status.
+int sync_status(elbm_handle* h) {
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, status_ptr(h), sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return ELBM_ERR_CUDA;
+    if (st != 0) {
+        e = cudaMemsetAsync(status_ptr(h), 0, sizeof(int), h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return ELBM_ERR_CUDA;
+        return ELBM_ERR_NONPHYSICAL;
+    }
+    return ELBM_OK;
+}
+
+int finalize_to_host(elbm_handle* h, const double* partials, int nb, double out[5]) {
+    finalize_kernel<<<1, 256, 0, h->stream>>>(partials, nb, totals_ptr(h));
+    ++h->launches;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, totals_ptr(h), 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return ELBM_ERR_CUDA;
+    return sync_status(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+int elbm_create(const elbm_params* prm, elbm_handle** out) {
+    if (!prm || !out) return ELBM_ERR_ARG;
+    *out = nullptr;
+    const elbm_params& p = *prm;
+    int D;
+    if (p.lattice == ELBM_D2Q9) D = 2;
+    else if (p.lattice == ELBM_D3Q27) D = 3;
+    else return ELBM_ERR_ARG;
+    if (p.nx < 1 || p.ny < 1 || p.nz < 1) return ELBM_ERR_ARG;
+    if (D == 2 && p.nz != 1) return ELBM_ERR_ARG;
+    const long long N = (long long)p.nx * p.ny * p.nz;
+    if (N > (1LL << 31)) return ELBM_ERR_UNSUPPORTED;
+    if (!(std::isfinite(p.gamma) && p.gamma > 1.0)) return ELBM_ERR_ARG;
+    if (!finite_pos(p.Pr) || !finite_pos(p.mu0) || !finite_pos(p.T0) || !std::isfinite(p.mu_exp))
+        return ELBM_ERR_ARG;
+    for (int k = 0; k < 6; ++k)
+        if (p.bc[k] != ELBM_BC_PERIODIC && p.bc[k] != ELBM_BC_ZEROGRAD) return ELBM_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if ((p.bc[2 * a] == ELBM_BC_PERIODIC) != (p.bc[2 * a + 1] == ELBM_BC_PERIODIC)) return ELBM_ERR_ARG;
+    if (p.store < ELBM_F64 || p.store > ELBM_BF16DEV) return ELBM_ERR_ARG;
+    if (p.deriv != ELBM_DERIV_UPWIND && p.deriv != ELBM_DERIV_CENTRAL) return ELBM_ERR_ARG;
+    const bool dev = p.store == ELBM_F16DEV || p.store == ELBM_BF16DEV;
+    if (dev && (!finite_pos(p.rho_ref) || !finite_pos(p.T_ref) || p.T_ref >= 1.0)) return ELBM_ERR_ARG;
+
+    elbm_handle* h = new (std::nothrow) elbm_handle();
+    if (!h) return ELBM_ERR_ARG;
+    h->prm = p;
+    h->D = D;
+    h->Q = D == 3 ? 27 : 9;
+    h->N = N;
+    h->ops = pick_ops(D, p.store);
+    h->kernel = ELBM_KERNEL_FUSED;
+
+    KParams& k = h->kp;
+    std::memset(&k, 0, sizeof(k));
+    k.nx = p.nx;
+    k.ny = p.ny;
+    k.nz = p.nz;
+    k.per_x = p.bc[0] == ELBM_BC_PERIODIC;
+    k.per_y = p.bc[2] == ELBM_BC_PERIODIC;
+    k.per_z = p.bc[4] == ELBM_BC_PERIODIC;
+    k.N = N;
+    k.gm1 = p.gamma - 1.0;
+    k.Pr = p.Pr;
+    k.mu0 = p.mu0;
+    k.T0 = p.T0;
+    k.mu_exp = p.mu_exp;
+    k.deriv = p.deriv;
+    k.tz = p.nz < 32 ? p.nz : 32;
+    if (dev) rest_state(D, p.rho_ref, p.T_ref, p.gamma, k.rest32);
+
+    h->pop_bytes = (size_t)2 * h->Q * (size_t)N * h->ops->value_bytes;
+    AuxLayout& a = h->aux;
+    a.max_blocks = h->ops->max_blocks(k);
+    size_t off = 0;
+    a.status = off;
+    off = align_up(off + sizeof(int));
+    a.totals = off;
+    off = align_up(off + 8 * sizeof(double));
+    a.partials = off;
+    off = align_up(off + 2 * 5 * sizeof(double) * (size_t)a.max_blocks);
+    a.qfield = off;
+    off = align_up(off + (size_t)D * N * h->ops->real_bytes);
+    a.staging = off;
+    off = align_up(off + (size_t)5 * N * sizeof(double));
+    a.bytes = off;
+    *out = h;
+    return ELBM_OK;
+}
+
+int elbm_bytes_required(const elbm_handle* h, size_t* pop_bytes, size_t* aux_bytes) {
+    if (!h) return ELBM_ERR_ARG;
+    if (pop_bytes) *pop_bytes = h->pop_bytes;
+    if (aux_bytes) *aux_bytes = h->aux.bytes;
+    return ELBM_OK;
+}
+
+int elbm_bind(elbm_handle* h, void* pop_a, void* pop_b, void* aux, void* stream) {
+    if (!h || !pop_a || !pop_b || !aux || pop_a == pop_b) return ELBM_ERR_ARG;
+    if (((uintptr_t)pop_a | (uintptr_t)pop_b | (uintptr_t)aux) % kAlign) return ELBM_ERR_ARG;
+    h->pop[0] = pop_a;
+    h->pop[1] = pop_b;
+    h->auxp = (char*)aux;
+    h->stream = (cudaStream_t)stream;
+    h->cur = 0;
+    h->bound = true;
+    return cuda_status(cudaMemsetAsync(status_ptr(h), 0, sizeof(int), h->stream));
+}
+
+int elbm_set_fields_device(elbm_handle* h, const double* rho, const double* u, const double* T) {
+    if (!h || !h->bound || !rho || !u || !T) return ELBM_ERR_ARG;
+    h->cur = 0;
+    h->steps = 0;
+    return cuda_status(h->ops->init(h->kp, rho, u, T, h->pop[0], status_ptr(h), h->stream, &h->launches));
+}
+
+int elbm_set_fields(elbm_handle* h, const double* rho, const double* u, const double* T) {
+    if (!h || !h->bound || !rho || !u || !T) return ELBM_ERR_ARG;
+    const size_t N = (size_t)h->N;
+    double* st = staging(h);
+    cudaError_t e = cudaMemcpyAsync(st, rho, N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(st + N, u, (size_t)h->D * N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(st + (1 + h->D) * N, T, N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return ELBM_ERR_CUDA;
+    int rc = elbm_set_fields_device(h, st, st + N, st + (1 + h->D) * N);
+    if (rc != ELBM_OK) return rc;
+    return sync_status(h);
+}
+
+int elbm_step(elbm_handle* h, int nsteps) {
+    if (!h || !h->bound || nsteps < 0) return ELBM_ERR_ARG;
+    for (int s = 0; s < nsteps; ++s) {
+        const void* src = h->pop[h->cur];
+        void* dst = h->pop[1 - h->cur];
+        cudaError_t e;
+        if (h->kernel == ELBM_KERNEL_TWOPASS)
+            e = h->ops->step_twopass(h->kp, src, dst, h->auxp + h->aux.qfield, step_partials(h), &h->step_blocks,
+                                     status_ptr(h), h->stream, &h->launches);
+        else
+            e = h->ops->step_fused(h->kp, src, dst, step_partials(h), &h->step_blocks, status_ptr(h), h->stream,
+                                   &h->launches);
+        if (e != cudaSuccess) return ELBM_ERR_CUDA;
+        h->cur = 1 - h->cur;
+        ++h->steps;
+    }
+    return ELBM_OK;
+}
+
+int elbm_get_fields_device(elbm_handle* h, double* rho, double* u, double* T) {
+    if (!h || !h->bound || !rho || !u || !T) return ELBM_ERR_ARG;
+    return cuda_status(h->ops->fields(h->kp, h->pop[h->cur], rho, u, T, status_ptr(h), h->stream, &h->launches));
+}
+
+int elbm_get_fields(elbm_handle* h, double* rho, double* u, double* T) {
+    if (!h || !h->bound || !rho || !u || !T) return ELBM_ERR_ARG;
+    const size_t N = (size_t)h->N;
+    double* st = staging(h);
+    int rc = elbm_get_fields_device(h, st, st + N, st + (1 + h->D) * N);
+    if (rc != ELBM_OK) return rc;
+    cudaError_t e = cudaMemcpyAsync(rho, st, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(u, st + N, (size_t)h->D * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(T, st + (1 + h->D) * N, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return ELBM_ERR_CUDA;
+    return sync_status(h);
+}
+
+int elbm_conservation(elbm_handle* h, double out[5]) {
+    if (!h || !h->bound || !out) return ELBM_ERR_ARG;
+    int nb = 0;
+    cudaError_t e = h->ops->conservation(h->kp, h->pop[h->cur], query_partials(h), &nb, h->stream, &h->launches);
+    if (e != cudaSuccess) return ELBM_ERR_CUDA;
+    return finalize_to_host(h, query_partials(h), nb, out);
+}
+
+int elbm_step_totals(elbm_handle* h, double out[5]) {
+    if (!h || !h->bound || !out) return ELBM_ERR_ARG;
+    if (h->steps == 0) return ELBM_ERR_ARG;
+    return finalize_to_host(h, step_partials(h), h->step_blocks, out);
+}
+
+int elbm_set_kernel(elbm_handle* h, int kernel) {
+    if (!h || (kernel != ELBM_KERNEL_FUSED && kernel != ELBM_KERNEL_TWOPASS)) return ELBM_ERR_ARG;
+    h->kernel = kernel;
+    return ELBM_OK;
+}
+
+int elbm_set_tile_z(elbm_handle* h, int tz) {
+    if (!h || tz < 1) return ELBM_ERR_ARG;
+    KParams k = h->kp;
+    k.tz = tz < h->prm.nz ? tz : h->prm.nz;
+    if (h->ops->max_blocks(k) > h->aux.max_blocks) return ELBM_ERR_ARG;   // partials would not fit
+    h->kp.tz = k.tz;
+    return ELBM_OK;
+}
+
+int elbm_get_populations(elbm_handle* h, void* host_dst) {
+    if (!h || !h->bound || !host_dst) return ELBM_ERR_ARG;
+    cudaError_t e = cudaMemcpyAsync(host_dst, h->pop[h->cur], h->pop_bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return ELBM_ERR_CUDA;
+    return sync_status(h);
+}
+
+int elbm_set_populations(elbm_handle* h, const void* host_src) {
+    if (!h || !h->bound || !host_src) return ELBM_ERR_ARG;
+    cudaError_t e = cudaMemcpyAsync(h->pop[h->cur], host_src, h->pop_bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return ELBM_ERR_CUDA;
+    return sync_status(h);
+}
+
+int elbm_sync(elbm_handle* h) {
+    if (!h || !h->bound) return ELBM_ERR_ARG;
+    return sync_status(h);
+}
+
+long long elbm_steps_done(const elbm_handle* h) { return h ? h->steps : -1; }
+
+long long elbm_launch_count(const elbm_handle* h) { return h ? h->launches : -1; }
+
+int elbm_velocity(int lattice, int i, int c[3]) {
+    const int Q = lattice == ELBM_D3Q27 ? 27 : (lattice == ELBM_D2Q9 ? 9 : 0);
+    if (!Q || i < 0 || i >= Q || !c) return ELBM_ERR_ARG;
+    c[0] = i % 3 - 1;
+    c[1] = (i / 3) % 3 - 1;
+    c[2] = Q == 27 ? i / 9 - 1 : 0;
+    return ELBM_OK;
+}
+
+int elbm_destroy(elbm_handle* h) {
+    delete h;
+    return ELBM_OK;
+}
+
+const char* elbm_status_str(int code) {
+    switch (code) {
+        case ELBM_OK: return "ok";
+        case ELBM_ERR_ARG: return "invalid argument";
+        case ELBM_ERR_UNSUPPORTED: return "unsupported combination";
+        case ELBM_ERR_CUDA: return "CUDA runtime error";
+        case ELBM_ERR_NONPHYSICAL: return "non-physical state (non-finite, rho <= 0 or T <= 0)";
+        case ELBM_ERR_TIMEOUT: return "bounded device wait timed out";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

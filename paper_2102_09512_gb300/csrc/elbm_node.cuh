@@ -1,0 +1,319 @@
+// Per-node arithmetic of the two-population compressible LB step, for sm_103a.
+//
+// Everything here acts on the 2Q populations of ONE node held in registers:
+// moments (Eqs. density, momentum, energy, P), temperature from the total energy
+// (Eqs. U, E with constant Cv = 1/(gamma-1), R = 1), the anomaly Q~_aaa
+// (Eq. anomalya), the relaxation rates (Eqs. mu, Pr), the extended f-equilibrium
+// (Eqs. productform, extf, Pa_star), the operator product-form g-equilibrium
+// (Eq. geq_i) in closed form, the quasi-equilibrium g* (Eqs. gstar, qstar1) and
+// the BGK relaxation (Eqs. fLBGK, gLBGK).
+//
+// Direction i = a + 3b + 9c with (c_x, c_y, c_z) = (a-1, b-1, c-1); D2Q9 uses
+// i = a + 3b.  All loops over directions are fully unrolled, so every index is a
+// compile-time constant and the populations stay in registers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace elbm {
+
+enum StoreKind { ST_F64 = 0, ST_F32 = 1, ST_F16DEV = 2, ST_BF16DEV = 3 };
+
+// Kernel parameters, passed by value (__grid_constant__).
+struct KParams {
+    int nx, ny, nz;
+    int per_x, per_y, per_z;     // 1: periodic axis, 0: zero-gradient (clamped)
+    long long N;                 // nx * ny * nz
+    double gm1;                  // gamma - 1  (so Cv = 1 / gm1)
+    double Pr, mu0, T0, mu_exp;
+    int deriv;                   // 0 upwind, 1 central
+    int tz;                      // z-segment length of the fused 3D kernel
+    float rest32[54];            // rest-state populations (f then g) for deviation stores
+};
+
+// ---------------------------------------------------------------------------
+// Storage codecs: load a stored value as arithmetic type R, store R.
+// ---------------------------------------------------------------------------
+template <int ST> struct Codec;
+
+template <> struct Codec<ST_F64> {
+    using S = double;
+    using R = double;
+    __device__ __forceinline__ static R load(const S* p, size_t k, float) { return p[k]; }
+    __device__ __forceinline__ static R dec(S v, float) { return v; }
+    __device__ __forceinline__ static S enc(R v, float) { return v; }
+};
+template <> struct Codec<ST_F32> {
+    using S = float;
+    using R = float;
+    __device__ __forceinline__ static R load(const S* p, size_t k, float) { return p[k]; }
+    __device__ __forceinline__ static R dec(S v, float) { return v; }
+    __device__ __forceinline__ static S enc(R v, float) { return v; }
+};
+template <> struct Codec<ST_F16DEV> {
+    using S = __half;
+    using R = float;
+    __device__ __forceinline__ static R dec(S v, float rest) { return rest + __half2float(v); }
+    __device__ __forceinline__ static R load(const S* p, size_t k, float rest) { return dec(p[k], rest); }
+    __device__ __forceinline__ static S enc(R v, float rest) { return __float2half_rn(v - rest); }
+};
+template <> struct Codec<ST_BF16DEV> {
+    using S = __nv_bfloat16;
+    using R = float;
+    __device__ __forceinline__ static R dec(S v, float rest) { return rest + __bfloat162float(v); }
+    __device__ __forceinline__ static R load(const S* p, size_t k, float rest) { return dec(p[k], rest); }
+    __device__ __forceinline__ static S enc(R v, float rest) { return __float2bfloat16_rn(v - rest); }
+};
+
+// ---------------------------------------------------------------------------
+// Lattice
+// ---------------------------------------------------------------------------
+template <int D> struct Lat {
+    static constexpr int Q = (D == 3) ? 27 : 9;
+    static constexpr int NC = (D == 3) ? 3 : 1;      // number of c_z values
+};
+__host__ __device__ constexpr int cx_of(int i) { return i % 3 - 1; }
+__host__ __device__ constexpr int cy_of(int i) { return (i / 3) % 3 - 1; }
+template <int D> __host__ __device__ constexpr int cz_of(int i) { return D == 3 ? i / 9 - 1 : 0; }
+
+// Index mapping of one axis: periodic wrap or zero-gradient clamp (the ghost is a
+// copy of the adjacent interior node).  Valid for x in [-1, n].
+__device__ __forceinline__ int map_axis(int x, int n, int periodic) {
+    if (x < 0) return periodic ? x + n : 0;
+    if (x >= n) return periodic ? x - n : n - 1;
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// Moments
+// ---------------------------------------------------------------------------
+template <typename R> struct Moments {
+    R rho, ux, uy, uz, T;
+    R Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;   // sum c c f (pre-collision)
+};
+
+// rho, rho u and the pressure tensor from f; rho E from g; T from E = Cv T + u^2/2.
+template <int D, typename R, bool FULL>
+__device__ __forceinline__ void node_moments(const R* f, const R* g, R gm1, Moments<R>& m) {
+    constexpr int NC = Lat<D>::NC;
+    // per (b, c) row sums over c_x
+    R t[3][3], d[3][3], e[3][3];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int i0 = 3 * b + 9 * c;
+            R lo = f[i0], mid = f[i0 + 1], hi = f[i0 + 2];
+            e[b][c] = hi + lo;
+            d[b][c] = hi - lo;
+            t[b][c] = e[b][c] + mid;
+        }
+    R rho = 0, jx = 0, Pxx = 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) { rho += t[b][c]; jx += d[b][c]; Pxx += e[b][c]; }
+    R tyh = 0, tyl = 0, dyh = 0, dyl = 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) { tyh += t[2][c]; tyl += t[0][c]; dyh += d[2][c]; dyl += d[0][c]; }
+    R jy = tyh - tyl, Pyy = tyh + tyl, Pxy = dyh - dyl;
+    R jz = 0, Pzz = 0, Pxz = 0, Pyz = 0;
+    if (D == 3) {
+        R tzh = 0, tzl = 0, dzh = 0, dzl = 0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) { tzh += t[b][2]; tzl += t[b][0]; dzh += d[b][2]; dzl += d[b][0]; }
+        jz = tzh - tzl;
+        Pzz = tzh + tzl;
+        Pxz = dzh - dzl;
+        Pyz = (t[2][2] - t[0][2]) - (t[2][0] - t[0][0]);
+    }
+    R rE = 0;
+#pragma unroll
+    for (int i = 0; i < Lat<D>::Q; ++i) rE += g[i];
+    const R inv = R(1) / rho;
+    m.rho = rho;
+    m.ux = jx * inv;
+    m.uy = jy * inv;
+    m.uz = jz * inv;
+    const R u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
+    m.T = (rE * inv - R(0.5) * u2) * gm1;
+    if (FULL) {
+        m.Pxx = Pxx; m.Pyy = Pyy; m.Pzz = Pzz;
+        m.Pxy = Pxy; m.Pxz = Pxz; m.Pyz = Pyz;
+    }
+}
+
+// Q~_aaa = rho u_a (1 - 3T - u_a^2)  (Eq. anomalya, R = 1)
+template <typename R>
+__device__ __forceinline__ R anomaly(R rho, R ua, R T) {
+    return rho * ua * (R(1) - R(3) * T - ua * ua);
+}
+
+// Discrete derivative of Q~_aaa at a node from its own value and the two axis
+// neighbours: upwind by the sign of u_a at the node (strict '>'), or central.
+template <typename R>
+__device__ __forceinline__ R dQ(int deriv, R ua, R qm, R q0, R qp) {
+    if (deriv) return R(0.5) * (qp - qm);
+    return ua > R(0) ? (q0 - qm) : (qp - q0);
+}
+
+// Unphysical-state test used to latch ELBM_ERR_NONPHYSICAL.
+template <typename R>
+__device__ __forceinline__ bool nonphysical(const Moments<R>& m) {
+    return !(m.rho > R(0)) || !(m.T > R(0)) || !isfinite(m.rho) || !isfinite(m.T) ||
+           !isfinite(m.ux) || !isfinite(m.uy) || !isfinite(m.uz);
+}
+
+// ---------------------------------------------------------------------------
+// Equilibria and collision
+// ---------------------------------------------------------------------------
+// Psi triplet at (xi, P), indexed a = c + 1 (Eqs. phi0S, phiPlusS, phiMinusS).
+template <typename R>
+__device__ __forceinline__ void psi3(R xi, R P, R out[3]) {
+    out[0] = R(0.5) * (P - xi);
+    out[1] = R(1) - P;
+    out[2] = R(0.5) * (P + xi);
+}
+
+// Per-axis factors of g^eq.  Applying Psi_c(O, O^2) (Eq. Operator) to functions of
+// one velocity component u gives
+//   on 1:       phi_c = Psi_c(u, T + u^2)                      (as f^eq)
+//   on u^2/2:   psi_0 = u^2/2 - s,  psi_{+-1} = (s +- o)/2,
+//   with o = O(u^2/2) = T u + u^3/2 and s = O^2(u^2/2) = T^2 + (5/2) T u^2 + u^4/2.
+// With E = Cv T + sum_b u_b^2/2 this gives
+//   g^eq_i = rho [ Cv T phi_x phi_y phi_z + psi_x phi_y phi_z + phi_x psi_y phi_z
+//                  + phi_x phi_y psi_z ].
+template <typename R>
+__device__ __forceinline__ void gfactors(R u, R T, R phi[3], R ps[3]) {
+    const R u2 = u * u;
+    psi3(u, T + u2, phi);
+    const R o = T * u + R(0.5) * u2 * u;
+    const R s = T * T + R(2.5) * T * u2 + R(0.5) * u2 * u2;
+    ps[0] = R(0.5) * (s - o);
+    ps[1] = R(0.5) * u2 - s;
+    ps[2] = R(0.5) * (s + o);
+}
+
+// Equilibria f^eq and g^eq of (rho, u, T) into f, g (used for initialisation and
+// for the rest state of the deviation stores).
+template <int D, typename R>
+__device__ __forceinline__ void equilibria(R rho, R ux, R uy, R uz, R T, R Cv, R* f, R* g) {
+    R X[3], Y[3], Z[3], px[3], py[3], pz[3], sx[3], sy[3], sz[3];
+    gfactors(ux, T, X, sx);
+    gfactors(uy, T, Y, sy);
+    if (D == 3) gfactors(uz, T, Z, sz);
+    else { Z[0] = Z[2] = 0; Z[1] = 1; sz[0] = sz[1] = sz[2] = 0; }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { px[a] = X[a]; }
+    const R CvT = Cv * T;
+#pragma unroll
+    for (int c = 0; c < Lat<D>::NC; ++c) {
+        const int cc = (D == 3) ? c : 1;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const R A = Y[b] * Z[cc];
+            const R B = sy[b] * Z[cc] + Y[b] * sz[cc];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int i = a + 3 * b + 9 * c;
+                f[i] = rho * px[a] * A;
+                g[i] = rho * ((CvT * X[a] + sx[a]) * A + X[a] * B);
+            }
+        }
+    }
+}
+
+// One collision in place.  D_a is the discrete derivative of Q~_aaa at the node.
+template <int D, typename R>
+__device__ __forceinline__ void collide(R* f, R* g, const Moments<R>& m, R Dx, R Dy, R Dz,
+                                        const KParams& p) {
+    const R rho = m.rho, T = m.T, ux = m.ux, uy = m.uy, uz = m.uz;
+    // relaxation rates (Eqs. mu, Pr) from the local pressure P = rho T
+    R mu = R(p.mu0);
+    if (p.mu_exp != 0.0) mu = mu * pow(T / R(p.T0), R(p.mu_exp));
+    const R P = rho * T;
+    const R w = R(2) * P / (R(2) * mu + P);
+    const R Pr = R(p.Pr);
+    const R w1 = R(2) * Pr * w / (R(2) - w + Pr * w);
+    const R Cv = R(1) / R(p.gm1);
+
+    // extended f-equilibrium (Eqs. Pa_star, extf)
+    const R k = (R(2) - w) / (R(2) * rho * w);
+    R X[3], Y[3], Z[3];
+    psi3(ux, T + ux * ux + k * Dx, X);
+    psi3(uy, T + uy * uy + k * Dy, Y);
+    if (D == 3) psi3(uz, T + uz * uz + k * Dz, Z);
+    else { Z[0] = Z[2] = 0; Z[1] = 1; }
+#pragma unroll
+    for (int c = 0; c < Lat<D>::NC; ++c) {
+        const int cc = (D == 3) ? c : 1;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const R yz = rho * Y[b] * Z[cc];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int i = a + 3 * b + 9 * c;
+                f[i] = f[i] + w * (X[a] * yz - f[i]);
+            }
+        }
+    }
+
+    // g-equilibrium (Eq. geq_i) relaxed with omega_1
+    R gx[3], gy[3], gz[3], sx[3], sy[3], sz[3];
+    gfactors(ux, T, gx, sx);
+    gfactors(uy, T, gy, sy);
+    if (D == 3) gfactors(uz, T, gz, sz);
+    else { gz[0] = gz[2] = 0; gz[1] = 1; sz[0] = sz[1] = sz[2] = 0; }
+    const R CvT = Cv * T;
+    R ax[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ax[a] = CvT * gx[a] + sx[a];
+#pragma unroll
+    for (int c = 0; c < Lat<D>::NC; ++c) {
+        const int cc = (D == 3) ? c : 1;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const R A = rho * gy[b] * gz[cc];
+            const R B = rho * (sy[b] * gz[cc] + gy[b] * sz[cc]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int i = a + 3 * b + 9 * c;
+                const R geq = ax[a] * A + gx[a] * B;
+                g[i] = g[i] + w1 * (geq - g[i]);
+            }
+        }
+    }
+
+    // quasi-equilibrium (Eqs. gstar, qstar1): q* - q^eq = u.(P - P^eq + div Q~ / 2),
+    // P^eq = rho T I + rho u u, div Q~ = diag(D); only |c_i| = 1 populations change,
+    // g_i += (omega - omega_1)(g^eq_i - g*_i) = -(omega - omega_1) c_i.(q* - q^eq) / 2.
+    const R rT = rho * T;
+    const R dxx = m.Pxx - rT - rho * ux * ux, dyy = m.Pyy - rT - rho * uy * uy;
+    const R dxy = m.Pxy - rho * ux * uy;
+    R dqx = ux * dxx + uy * dxy + R(0.5) * ux * Dx;
+    R dqy = ux * dxy + uy * dyy + R(0.5) * uy * Dy;
+    R dqz = 0;
+    if (D == 3) {
+        const R dzz = m.Pzz - rT - rho * uz * uz;
+        const R dxz = m.Pxz - rho * ux * uz, dyz = m.Pyz - rho * uy * uz;
+        dqx += uz * dxz;
+        dqy += uz * dyz;
+        dqz = ux * dxz + uy * dyz + uz * dzz + R(0.5) * uz * Dz;
+    }
+    const R h = R(0.5) * (w - w1);
+    // unit-speed directions: (-1,0,0)=a0, (+1,0,0)=a2 on row b=1, c=centre
+    constexpr int C0 = (D == 3) ? 9 : 0;
+    g[C0 + 3 + 0] += h * dqx;
+    g[C0 + 3 + 2] -= h * dqx;
+    g[C0 + 1] += h * dqy;        // (0,-1,0)
+    g[C0 + 7] -= h * dqy;        // (0,+1,0)
+    if (D == 3) {
+        g[4] += h * dqz;         // (0,0,-1)
+        g[22] -= h * dqz;        // (0,0,+1)
+    }
+}
+
+}  // namespace elbm

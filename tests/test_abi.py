@@ -1,0 +1,87 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports every
+symbol that include/elbm.h declares, and validates parameters on the host
+(elbm_create and elbm_bytes_required make no CUDA call)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2102_09512_gb300 import build as B
+    B.build()
+    from paper_2102_09512_gb300 import elbm as E
+    return E
+
+
+def declared_symbols():
+    with open(os.path.join(ROOT, "include", "elbm.h")) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(elbm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_symbols()
+    assert len(names) >= 20
+    lib = L.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding wraps each of them under the same name
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_status_strings(L):
+    for code in (0, -1, -2, -3, -4, -5):
+        assert L.elbm_status_str(code)
+
+
+def test_velocity_table(L):
+    for lat, Q in ((L.ELBM_D2Q9, 9), (L.ELBM_D3Q27, 27)):
+        cs = {L.elbm_velocity(lat, i) for i in range(Q)}
+        assert len(cs) == Q
+        for i in range(Q):
+            c = L.elbm_velocity(lat, i)
+            assert i == (c[0] + 1) + 3 * (c[1] + 1) + (9 * (c[2] + 1) if Q == 27 else 0)
+
+
+def test_create_and_sizes(L):
+    p = L.make_params(3, 64, 48, 40, store="f32")
+    h = L.elbm_create(p)
+    pop, aux = L.elbm_bytes_required(h)
+    assert pop == 2 * 27 * 64 * 48 * 40 * 4
+    assert aux >= 3 * 64 * 48 * 40 * 4 + 5 * 64 * 48 * 40 * 8
+    L.elbm_destroy(h)
+    p = L.make_params(2, 100, 30, 1, store="f16dev")
+    h = L.elbm_create(p)
+    pop, _ = L.elbm_bytes_required(h)
+    assert pop == 2 * 9 * 3000 * 2
+    L.elbm_destroy(h)
+
+
+@pytest.mark.parametrize("field,value", [
+    ("lattice", 19), ("nx", 0), ("nz", 2), ("gamma", 1.0), ("Pr", 0.0), ("mu0", -1.0),
+    ("T0", 0.0), ("store", 7), ("deriv", 3),
+])
+def test_create_rejects_bad_arguments(L, field, value):
+    p = L.make_params(2, 16, 16, 1)
+    setattr(p, field, value)
+    with pytest.raises(L.ElbmError) as ei:
+        L.elbm_create(p)
+    assert ei.value.code == L.ELBM_ERR_ARG
+
+
+def test_create_rejects_mixed_axis_bc(L):
+    p = L.make_params(2, 16, 16, 1, bc=(0, 1, 0, 0, 0, 0))
+    with pytest.raises(L.ElbmError):
+        L.elbm_create(p)
+
+
+def test_unbound_handle_is_rejected(L):
+    h = L.elbm_create(L.make_params(2, 16, 16, 1))
+    assert L.elbm_step(h, 1) == L.ELBM_ERR_ARG
+    L.elbm_destroy(h)

@@ -1,0 +1,273 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by
+element on the same seeded inputs.
+
+Tolerances (relative L2 over all nodes, all components for u): FP64 store 1e-12,
+FP32 1e-5, FP16/BF16 deviation stores 1e-3, over the stated number of steps.
+Grids are chosen ragged against the 32 x 8 tiles of the fused kernels and, in 3D,
+against the z segments.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2102_09512_gb300 import cases as C
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16dev": 1e-3, "bf16dev": 1e-3}
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2102_09512_gb300 import build as B
+    B.build()
+    O.build()
+    O.set_threads(0)
+    from paper_2102_09512_gb300 import elbm
+    return elbm
+
+
+def oparams(c, **kw):
+    d = dict(D=c.D, nx=c.nx, ny=c.ny, nz=c.nz, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0,
+             mu_exp=c.mu_exp, bc=c.bc)
+    d.update(kw)
+    return O.Params(**d)
+
+
+_ORACLE = {}
+
+
+def oracle_fields(key, c, steps, **kw):
+    if key not in _ORACLE:
+        s = O.init(oparams(c, **kw), c.rho, c.u, c.T)
+        O.step(s, steps)
+        _ORACLE[key] = O.fields(s)
+    return _ORACLE[key]
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def gpu_fields(E, c, steps, store, kernel=0, deriv=0, tz=None):
+    g = E.Solver.from_case(c, store=store, deriv=deriv)
+    g.set_kernel(kernel)
+    if tz is not None:
+        g.set_tile_z(tz)
+    g.step(steps)
+    out = g.fields()
+    g.close()
+    return out
+
+
+def assert_parity(got, ref, tol, label=""):
+    names = ("rho", "u", "T")
+    errs = {n: rel_l2(a, b) for n, a, b in zip(names, got, ref)}
+    for n in names:
+        assert errs[n] <= tol, (label, errs)
+    return errs
+
+
+CASES_2D = {
+    "periodic": lambda: C.random_smooth(2, 37, 29, 1, seed=11, mu0=0.01),
+    "zerograd": lambda: C.random_smooth(2, 45, 19, 1, seed=12, mu0=0.01, bc=(1, 1, 1, 1, 0, 0)),
+}
+CASES_3D = {
+    "periodic": lambda: C.random_smooth(3, 37, 21, 19, seed=21, mu0=0.01),
+    "zerograd": lambda: C.random_smooth(3, 20, 13, 17, seed=22, mu0=0.01, bc=(1, 1, 0, 0, 1, 1)),
+}
+
+
+@pytest.mark.parametrize("store", list(TOL))
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("case", list(CASES_2D))
+def test_d2q9_parity(E, case, kernel, store):
+    c = CASES_2D[case]()
+    steps = 100
+    ref = oracle_fields(("2d", case), c, steps)
+    assert_parity(gpu_fields(E, c, steps, store, kernel), ref, TOL[store], (case, kernel, store))
+
+
+@pytest.mark.parametrize("store", list(TOL))
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("case", list(CASES_3D))
+def test_d3q27_parity(E, case, kernel, store):
+    c = CASES_3D[case]()
+    steps = 40
+    ref = oracle_fields(("3d", case), c, steps)
+    assert_parity(gpu_fields(E, c, steps, store, kernel), ref, TOL[store], (case, kernel, store))
+
+
+@pytest.mark.parametrize("tz", [1, 5, 7, 64])
+def test_d3q27_z_segments(E, tz):
+    """The z-segment length of the fused kernel changes nothing but the schedule."""
+    c = CASES_3D["periodic"]()
+    ref = oracle_fields(("3d", "periodic"), c, 40)
+    assert_parity(gpu_fields(E, c, 40, "f64", 0, tz=tz), ref, TOL["f64"], tz)
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_central_derivative_variant(E, D):
+    c = C.random_smooth(D, 33, 17, 9 if D == 3 else 1, seed=31, mu0=0.01)
+    ref = oracle_fields(("central", D), c, 30, deriv=1)
+    for store in ("f64", "f32"):
+        assert_parity(gpu_fields(E, c, 30, store, 0, deriv=1), ref, TOL[store], store)
+
+
+def test_power_law_viscosity(E):
+    c = C.random_smooth(3, 24, 17, 10, seed=41, mu0=0.01, mu_exp=0.76, dT=0.04)
+    ref = oracle_fields(("powerlaw",), c, 30)
+    for store in ("f64", "f32"):
+        assert_parity(gpu_fields(E, c, 30, store, 0), ref, TOL[store], store)
+
+
+def test_sod_tube_fp64_parity_and_exact_solution(E):
+    """Sod tube (Sec. III.B), 800 x 4, 500 steps, FP64: oracle parity, and the GPU
+    profile against the exact Riemann solution."""
+    import exact_riemann as R
+    c = C.sod(nx=800, ny=4, mu=0.015)
+    ref = oracle_fields(("sod",), c, 500)
+    got = gpu_fields(E, c, 500, "f64", 0)
+    assert_parity(got, ref, TOL["f64"])
+    rho = got[0].reshape(4, 800)[0]
+    ux = got[1][0].reshape(4, 800)[0]
+    xi = (np.arange(800) + 0.5 - 400.0) / 500.0
+    re, ue, _ = R.sample(xi, 1.0, 0.0, 0.15, 0.125, 0.0, 0.015)
+    assert np.mean(np.abs(rho - re)) < 4.5e-3
+    assert np.mean(np.abs(ux - ue)) < 2.0e-3
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_conservation_totals(E, D):
+    """FP64 totals of the GPU state equal the oracle's; the totals accumulated inside
+    the step kernel equal the totals of the state the step started from; under
+    periodic boundaries they do not drift."""
+    c = C.random_smooth(D, 37, 21, 19 if D == 3 else 1, seed=51, mu0=0.01)
+    s = O.init(oparams(c), c.rho, c.u, c.T)
+    t0 = O.conservation(s)
+    g = E.Solver.from_case(c, store="f64")
+    assert np.allclose(g.conservation(), t0, rtol=1e-14, atol=1e-14 * abs(t0[0]))
+    for kernel in (0, 1):
+        g.set_kernel(kernel)
+        before = g.conservation()
+        g.step(1)
+        assert np.allclose(g.step_totals(), before, rtol=1e-13, atol=1e-13 * abs(t0[0]))
+    g.step(20)
+    t1 = g.conservation()
+    scale = np.array([t0[0]] * 4 + [t0[4]])
+    assert np.all(np.abs(t1 - t0) / scale < 1e-13)
+    g.close()
+
+
+def test_checkpoint_restart_is_bitwise(E):
+    c = C.random_smooth(3, 21, 13, 9, seed=61, mu0=0.01)
+    for store in ("f64", "f32", "f16dev"):
+        a = E.Solver.from_case(c, store=store)
+        a.step(10)
+        snap = a.get_populations()
+        a.step(10)
+        ref = a.fields()
+        b = E.Solver.from_case(c, store=store)
+        b.set_populations(snap)
+        b.step(10)
+        got = b.fields()
+        for x, y in zip(got, ref):
+            assert np.array_equal(x, y), store
+        a.close()
+        b.close()
+
+
+def test_fused_and_twopass_agree(E):
+    c = CASES_3D["periodic"]()
+    for store, tol in (("f64", 1e-14), ("f32", 1e-6)):
+        a = gpu_fields(E, c, 20, store, 0)
+        b = gpu_fields(E, c, 20, store, 1)
+        for x, y in zip(a, b):
+            assert rel_l2(x, y) <= tol, store
+
+
+def test_nonphysical_state_is_reported_and_recoverable(E):
+    """A negative temperature (host-side fault injection) is latched on the device and
+    reported as ELBM_ERR_NONPHYSICAL; the handle and the context stay usable."""
+    c = C.random_smooth(2, 40, 24, 1, seed=71, mu0=0.01)
+    g = E.Solver.from_case(c, store="f32")
+    T = c.T.copy()
+    T.reshape(-1)[123] = -0.1
+    with pytest.raises(E.ElbmError) as ei:
+        g.set_fields(c.rho, c.u, T)
+    assert ei.value.code == E.ELBM_ERR_NONPHYSICAL
+    g.set_fields(c.rho, c.u, c.T)
+    g.step(5)
+    g.sync()
+    rho, _, _ = g.fields()
+    assert np.all(np.isfinite(rho))
+    g.close()
+
+
+def test_device_field_entry_points(E):
+    import torch
+    c = C.random_smooth(3, 19, 11, 7, seed=81, mu0=0.01)
+    g = E.Solver.from_case(c, store="f32")
+    rho = torch.tensor(c.rho.reshape(-1), device="cuda")
+    u = torch.tensor(c.u.reshape(-1), device="cuda")
+    T = torch.tensor(c.T.reshape(-1), device="cuda")
+    g.set_fields(rho, u, T)
+    g.step(3)
+    r2, u2, T2 = torch.empty_like(rho), torch.empty_like(u), torch.empty_like(T)
+    g.fields_device(r2, u2, T2)
+    h = g.fields()
+    torch.cuda.synchronize()
+    assert np.array_equal(r2.cpu().numpy(), h[0])
+    assert np.array_equal(T2.cpu().numpy(), h[2])
+    g.close()
+
+
+def _center_after_one_step(c, x, y, z):
+    """Oracle value at (x, y, z) after one step, computed on the 5^3 neighbourhood
+    (one step at a node depends on nodes at most two apart)."""
+    n = c.nx
+    idx = [(np.arange(-2, 3) + v) % n for v in (x, y, z)]
+    sub_rho = c.rho[np.ix_(idx[2], idx[1], idx[0])]
+    sub_T = c.T[np.ix_(idx[2], idx[1], idx[0])]
+    sub_u = np.stack([c.u[a][np.ix_(idx[2], idx[1], idx[0])] for a in range(3)])
+    p = O.Params(D=3, nx=5, ny=5, nz=5, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0,
+                 mu_exp=c.mu_exp, bc=(1, 1, 1, 1, 1, 1))
+    s = O.init(p, sub_rho, sub_u, sub_T)
+    O.step(s, 1)
+    r, u, T = O.fields(s)
+    k = 2 + 5 * (2 + 5 * 2)
+    return r[k], u[:, k], T[k]
+
+
+@pytest.mark.parametrize("store,tol", [("f32", 2e-6), ("f16dev", 2e-4)])
+def test_full_size_256_sampled_nodes(E, store, tol):
+    """At the bench's full size (D3Q27, 256^3, decaying-turbulence field, fused kernel)
+    sampled nodes after one step equal the oracle's one-by-one values, and the
+    totals are conserved over 5 steps."""
+    c = C.hit(256, seed=20210218)
+    g = E.Solver.from_case(c, store=store)
+    t0 = g.conservation()
+    g.step(1)
+    rho, u, T = g.fields()
+    rng = np.random.default_rng(5)
+    pts = rng.integers(0, 256, size=(12, 3))
+    pts[0] = (0, 0, 0)
+    pts[1] = (255, 255, 255)
+    for x, y, z in pts:
+        n = x + 256 * (y + 256 * z)
+        r_o, u_o, T_o = _center_after_one_step(c, x, y, z)
+        assert abs(rho[n] - r_o) <= tol * abs(r_o)
+        assert abs(T[n] - T_o) <= tol * abs(T_o)
+        assert np.max(np.abs(u[:, n] - u_o)) <= tol * 0.5
+    g.step(4)
+    t1 = g.conservation()
+    assert abs(t1[0] - t0[0]) / t0[0] < 1e-6
+    assert abs(t1[4] - t0[4]) / t0[4] < 1e-6
+    assert np.max(np.abs(t1[1:4] - t0[1:4])) / t0[0] < 1e-6
+    g.close()
