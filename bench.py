@@ -1,0 +1,366 @@
+"""Benchmark: D3Q27 two-population compressible LB updates per second (GLUPS) at
+256^3 on one GB300, for FP32, FP16- and BF16-deviation and FP64 population stores,
+with the HBM roofline fraction of the step kernel.
+
+Workload: decaying compressible turbulence (paper Sec. III.D) on a periodic 256^3
+D3Q27 box, Ma_t = 0.5, Re_lambda = 72, T0 = 0.15, gamma = 1.4, Pr = 0.7,
+mu = mu0 (T/T0)^0.76, synthetic initial field E(k) ~ k^4 exp(-2 (k/4)^2), seed
+20210218.  One bench step = one time step of the whole path (pull streaming,
+moments, anomaly derivative, both equilibria, quasi-equilibrium, BGK, store, and
+the per-step FP64 conservation totals) over all 16.8M nodes.  One update = both
+populations at one node for one step.
+
+Default: N = 1, 20 timed steps after 5 warm-up steps.  Under torchrun (N > 1)
+every rank runs an independent replica of the workload (the path needs no
+exchange between replicas; weak scaling).
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (a 32^3 box of the same generator) and prints the same
+JSON line with ``"impl": "reference"``.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIDE = 256
+BYTES_PER_UPDATE = {"f64": 864, "f32": 432, "f16dev": 216, "bf16dev": 216}
+METRIC = "D3Q27 two-pop GLUPS at 256^3: FP16-store vs FP32 vs FP64; % of HBM roofline"
+WORKLOAD = "D3Q27 decaying compressible turbulence 256^3, periodic, Ma_t=0.5, Re_lambda=72"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d and d[k]:
+                return float(d[k]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def _sources_digest():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2102_09512_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        e = d.get(kernel_key)
+        if e and e.get("sources_digest") == _sources_digest():
+            return float(e["dram_bytes_per_launch"])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(min_seconds=10.0, max_seconds=30.0):
+    """The FP64 oracle on the host cores on a 32^3 box of the same generator; returns
+    (GLUPS, threads, description)."""
+    import oracle as O
+    from paper_2102_09512_gb300 import cases as C
+
+    O.build()
+    threads = O.set_threads(os.cpu_count() or 1)
+    n = 32
+    c = C.hit(n)
+    p = O.Params(D=3, nx=n, ny=n, nz=n, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0, mu_exp=c.mu_exp, bc=c.bc)
+    s = O.init(p, c.rho, c.u, c.T)
+    O.step(s, 1)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        O.step(s, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or el >= max_seconds:
+            break
+    glups = n ** 3 * steps / el / 1e9
+    return glups, threads, f"D3Q27 32^3 box of the same turbulence generator, {steps} steps, {el:.1f} s"
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    per_step = []
+    import oracle as O
+    from paper_2102_09512_gb300 import cases as C
+    O.build()
+    threads = O.set_threads(os.cpu_count() or 1)
+    n = 32
+    c = C.hit(n)
+    p = O.Params(D=3, nx=n, ny=n, nz=n, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0, mu_exp=c.mu_exp, bc=c.bc)
+    s = O.init(p, c.rho, c.u, c.T)
+    for _ in range(args.warmup):
+        O.step(s, 1)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.step(s, 1)
+        per_step.append(time.perf_counter() - t0)
+    total = sum(per_step)
+    value = n ** 3 * args.steps / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "32^3 box, same generator"},
+        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": threads, "kind": "oracle",
+                         "sample": f"D3Q27 32^3 box of the same generator, {args.steps} steps"},
+        "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_store(E, torch, case, store, steps, warmup, stream):
+    """Device-resident timing of `steps` steps; returns (ms_per_step, launches, solver)."""
+    g = E.Solver.from_case(case, store=store, stream=stream)
+    g.step(warmup)
+    g.sync()
+    l0 = g.launches
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        g.step(steps)
+        e1.record(stream)
+    e1.synchronize()
+    g.sync()
+    ms = e0.elapsed_time(e1) / steps
+    return ms, g.launches - l0, g
+
+
+def time_e2e(E, torch, case, store, steps, stream):
+    """End-to-end through the C ABI with host buffers: upload the initial fields from
+    pinned host memory, take `steps` steps reading the step's conserved totals back
+    after each, download the final fields.  Returns (ms_per_step, h2d, d2h bytes/step)."""
+    import numpy as np
+    N = case.N
+    rho = torch.from_numpy(np.ascontiguousarray(case.rho.reshape(N))).pin_memory()
+    u = torch.from_numpy(np.ascontiguousarray(case.u.reshape(3 * N))).pin_memory()
+    T = torch.from_numpy(np.ascontiguousarray(case.T.reshape(N))).pin_memory()
+    out = [torch.empty(N, dtype=torch.float64).pin_memory(), torch.empty(3 * N, dtype=torch.float64).pin_memory(),
+           torch.empty(N, dtype=torch.float64).pin_memory()]
+    g = E.Solver(E.make_params(3, case.nx, case.ny, case.nz, case.gamma, case.Pr, case.mu0, case.T0, case.mu_exp,
+                               case.bc, store, 0, 1.0, case.T0), stream=stream)
+    # warm the path once
+    E._check(E.elbm_set_fields(g.h, rho, u, T), "elbm_set_fields")
+    g.step(2)
+    g.step_totals()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E._check(E.elbm_set_fields(g.h, rho, u, T), "elbm_set_fields")
+    for _ in range(steps):
+        g.step(1)
+        g.step_totals()
+    E._check(E.elbm_get_fields(g.h, out[0], out[1], out[2]), "elbm_get_fields")
+    el = time.perf_counter() - t0
+    g.close()
+    h2d = 5 * 8 * N / steps
+    d2h = (5 * 8 * N) / steps + 5 * 8
+    return 1e3 * el / steps, h2d, d2h
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--stores", default="f32,f16dev,bf16dev,f64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--size", type=int, default=N_SIDE, help="box side (the bench workload is 256)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2102_09512_gb300 import cases as C
+    from paper_2102_09512_gb300 import elbm as E
+
+    n_side = args.size
+    case = C.hit(n_side)
+    stream = torch.cuda.Stream()
+    stores = [s for s in args.stores.split(",") if s]
+    peak, peak_kind = _peak_hbm()
+    variants = {}
+    head = None
+    clocks = None
+    launches_head = None
+    for store in stores:
+        k = args.steps if store != "f64" else max(3, args.steps // 4)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(dev) if store == stores[0] and rank == 0 else None
+        if sampler:
+            sampler.start()
+        ms, launches, g = time_store(E, torch, case, store, k, args.warmup, stream)
+        if sampler:
+            clocks = sampler.stop()
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        totals = g.conservation()
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+        glups = ws * case.N / (ms * 1e-3) / 1e9
+        per_gpu_gbs = case.N / (ms * 1e-3) * BYTES_PER_UPDATE[store] / 1e9
+        variants[store] = {"glups": glups, "ms_per_step": ms, "timed_steps": k,
+                           "algorithmic_GBs_per_gpu": per_gpu_gbs,
+                           "hbm_frac": per_gpu_gbs / peak, "bytes_per_update": BYTES_PER_UPDATE[store],
+                           "kernel_launches_per_step": launches / k,
+                           "mass_total": float(totals[0]), "energy_total": float(totals[4])}
+        if head is None:
+            head = store
+            launches_head = launches
+    hs = variants[head]
+    if rank != 0:
+        dist.barrier() if ws > 1 else None
+        return 0
+
+    # end-to-end through the C ABI with host buffers (headline store)
+    e2e = None
+    if not args.no_e2e:
+        e2e_ms, h2d, d2h = time_e2e(E, torch, case, head, args.steps, stream)
+        e2e = {"value": ws * case.N / (e2e_ms * 1e-3) / 1e9, "unit": "GLUPS", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, cores, sample = cpu_oracle_sample()
+        cpu = {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle", "sample": sample}
+
+    kernel_key = f"fused3d_{head}_{n_side}"
+    traffic = _ncu_traffic(kernel_key)
+    roofline = {"bound": "hbm", "achieved": hs["algorithmic_GBs_per_gpu"], "peak": peak, "unit": "GB/s",
+                "frac": hs["algorithmic_GBs_per_gpu"] / peak, "peak_kind": peak_kind,
+                "traffic": traffic, "kernel": kernel_key,
+                "algorithmic_bytes_per_launch": BYTES_PER_UPDATE[head] * case.N}
+    line = {
+        "metric": METRIC, "value": hs["glups"], "unit": "GLUPS", "n_gpus": ws, "steps": hs["timed_steps"],
+        "warmup": args.warmup, "ms_per_step": hs["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if head != "f64" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if n_side == N_SIDE else WORKLOAD.replace("256^3", f"{n_side}^3"),
+                   "lattice": "D3Q27", "grid": [n_side] * 3, "store": head,
+                   "schedule": "fused", "l2": "inputs larger than L2 (3.6 GB FP32 store)",
+                   "parallelism": "replicas" if ws > 1 else "single-gpu"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_head,
+        "clocks": clocks, "variants": variants,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -20,6 +20,10 @@
  *    owns only the handle.  Population layout (structure of arrays): plane k of
  *    N values for k = 0..2Q-1, f planes first, then g planes; direction
  *    i = (c_x+1) + 3(c_y+1) + 9(c_z+1).  Device pointers must be 256-byte aligned.
+ *    The store holds the post-collision populations of the current time level
+ *    (streaming is a pull at the start of the next step); their moments rho,
+ *    rho u, rho E equal those of the post-stream state because the collision
+ *    conserves them.
  *  - Calls are asynchronous on the bound stream unless stated; functions that
  *    return host data synchronise the stream.
  *  - Errors: every function returns an elbm_status (0 = ELBM_OK).  Argument errors
@@ -118,9 +122,10 @@ int elbm_get_fields_device(elbm_handle *h, double *rho, double *u, double *T);
  * Synchronises. */
 int elbm_conservation(elbm_handle *h, double out[5]);
 
-/* The same totals of the state at the start of the last step, accumulated inside
- * that step's kernel (fused schedule; FP32 per thread, FP64 compensated across
- * threads).  Synchronises. */
+/* The same totals accumulated inside the last step's kernel from the populations
+ * it pulled (the state that step produced; the collision conserves the totals).
+ * FP64 stores: FP64 throughout; other stores: compensated sums in the arithmetic
+ * type per thread, FP64 across threads.  Synchronises. */
 int elbm_step_totals(elbm_handle *h, double out[5]);
 
 /* Selects the kernel schedule (elbm_kernel).  Results agree to rounding. */

@@ -238,9 +238,11 @@ def thermal_wave(D: int = 2, L: int = 64, A: float = 1e-4, rho0: float = 1.0, T0
 def random_smooth(D: int, nx: int, ny: int, nz: int = 1, seed: int = 0, rho0: float = 1.0,
                   T0: float = 0.15, drho: float = 0.05, du: float = 0.08, dT: float = 0.02,
                   modes: int = 4, gamma: float = 1.4, Pr: float = 0.71, mu0: float = 0.01,
-                  mu_exp: float = 0.0, bc=(0, 0, 0, 0, 0, 0)) -> Case:
-    """Smooth seeded random fields: each of rho, u_a, T is its base value plus a sum of
-    `modes` random Fourier modes (periodic on the box) scaled to the given amplitude."""
+                  mu_exp: float = 0.0, bc=(0, 0, 0, 0, 0, 0), u0=(0.0, 0.0, 0.0)) -> Case:
+    """Smooth seeded random fields: each of rho, u_a, T is its base value (u0 for the
+    velocity) plus a sum of `modes` random Fourier modes (periodic on the box) scaled
+    so that the perturbation never exceeds the given amplitude.  With |u0_a| > du every
+    velocity component keeps one sign everywhere."""
     rng = np.random.default_rng(seed)
     if D == 2:
         nz = 1
@@ -257,6 +259,6 @@ def random_smooth(D: int, nx: int, ny: int, nz: int = 1, seed: int = 0, rho0: fl
 
     rho = rho0 + field_(drho)
     T = T0 + field_(dT)
-    u = np.stack([field_(du) for _ in range(D)])
+    u = np.stack([u0[a] + field_(du) for a in range(D)])
     return Case("random_smooth", D, nx, ny, nz, rho, u, T, gamma=gamma, Pr=Pr, mu0=mu0, T0=T0,
                 mu_exp=mu_exp, bc=tuple(bc))

@@ -235,7 +235,8 @@ int elbm_set_fields_device(elbm_handle* h, const double* rho, const double* u, c
     if (!h || !h->bound || !rho || !u || !T) return ELBM_ERR_ARG;
     h->cur = 0;
     h->steps = 0;
-    return cuda_status(h->ops->init(h->kp, rho, u, T, h->pop[0], status_ptr(h), h->stream, &h->launches));
+    return cuda_status(h->ops->init(h->kp, rho, u, T, h->pop[0], h->pop[1], h->auxp + h->aux.qfield,
+                                    query_partials(h), status_ptr(h), h->stream, &h->launches));
 }
 
 int elbm_set_fields(elbm_handle* h, const double* rho, const double* u, const double* T) {

@@ -27,7 +27,8 @@ struct Ops {
     size_t real_bytes;    // bytes of the arithmetic type (Q~ field)
     int (*max_blocks)(const KParams& p);
     cudaError_t (*init)(const KParams& p, const double* rho, const double* u, const double* T,
-                        void* pop, int* status, cudaStream_t s, long long* launches);
+                        void* pop, void* spare, void* qfield, double* partials, int* status,
+                        cudaStream_t s, long long* launches);
     cudaError_t (*fields)(const KParams& p, const void* pop, double* rho, double* u, double* T,
                           int* status, cudaStream_t s, long long* launches);
     cudaError_t (*step_twopass)(const KParams& p, const void* src, void* dst, void* qfield,

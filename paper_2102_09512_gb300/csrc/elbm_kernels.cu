@@ -49,13 +49,16 @@ struct PullRows {
     int xs[3];             // x - c_x for a = c_x+1
 };
 
+// With PULL = false every direction is read at the node itself (no streaming);
+// that form is used once, to collide the initial state.
+template <bool PULL = true>
 __device__ __forceinline__ void pull_rows(const KParams& p, int x, int y, int z, PullRows& r) {
-    r.xs[0] = map_axis(x + 1, p.nx, p.per_x);
+    r.xs[0] = PULL ? map_axis(x + 1, p.nx, p.per_x) : x;
     r.xs[1] = x;
-    r.xs[2] = map_axis(x - 1, p.nx, p.per_x);
-    int ys[3] = {map_axis(y + 1, p.ny, p.per_y), y, map_axis(y - 1, p.ny, p.per_y)};
+    r.xs[2] = PULL ? map_axis(x - 1, p.nx, p.per_x) : x;
+    int ys[3] = {PULL ? map_axis(y + 1, p.ny, p.per_y) : y, y, PULL ? map_axis(y - 1, p.ny, p.per_y) : y};
     int zs[3] = {z, z, z};
-    if (kD == 3) {
+    if (kD == 3 && PULL) {
         zs[0] = map_axis(z + 1, p.nz, p.per_z);
         zs[2] = map_axis(z - 1, p.nz, p.per_z);
     }
@@ -239,6 +242,7 @@ __global__ void totals_kernel(const __grid_constant__ KParams p, const S* __rest
 // two-pass schedule
 // ---------------------------------------------------------------------------
 // Pass 1: Q~_aaa at every node from the pulled (post-stream) populations.
+template <bool PULL>
 __global__ void moments_kernel(const __grid_constant__ KParams p, const S* __restrict__ src,
                                R* __restrict__ qf) {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -247,7 +251,7 @@ __global__ void moments_kernel(const __grid_constant__ KParams p, const S* __res
     const int y = (int)((n / p.nx) % p.ny);
     const int z = (int)(n / ((long long)p.nx * p.ny));
     PullRows r;
-    pull_rows(p, x, y, z, r);
+    pull_rows<PULL>(p, x, y, z, r);
     R f[Q], g[Q];
     gather(p, src, r, f, g);
     Moments<R> m;
@@ -258,6 +262,7 @@ __global__ void moments_kernel(const __grid_constant__ KParams p, const S* __res
 }
 
 // Pass 2: pull, moments, derivative of Q~ from the field, collide, store.
+template <bool PULL>
 __global__ void collide_kernel(const __grid_constant__ KParams p, const S* __restrict__ src,
                                S* __restrict__ dst, const R* __restrict__ qf,
                                double* __restrict__ partials, int* __restrict__ status) {
@@ -269,7 +274,7 @@ __global__ void collide_kernel(const __grid_constant__ KParams p, const S* __res
         const int y = (int)((n / p.nx) % p.ny);
         const int z = (int)(n / ((long long)p.nx * p.ny));
         PullRows r;
-        pull_rows(p, x, y, z, r);
+        pull_rows<PULL>(p, x, y, z, r);
         R f[Q], g[Q];
         gather(p, src, r, f, g);
         Moments<R> m;
@@ -483,10 +488,20 @@ int max_blocks(const KParams& p) {
     return (int)m;
 }
 
+// The stored state is post-collision: after step n the store holds C(X_n), where
+// X_n is the post-stream state of the method and C the collision, and a step is
+// pull (X_{n+1} = S(C(X_n))) followed by collide.  Initialisation therefore writes
+// X_0 = (f^eq, g^eq) into the spare store and collides it in place of streaming.
+// Moments of C(X_n) equal those of X_n (the collision conserves them), so field
+// extraction and totals read each node's own values.
 cudaError_t launch_init(const KParams& p, const double* rho, const double* u, const double* T, void* pop,
-                        int* status, cudaStream_t s, long long* launches) {
-    init_kernel<<<blocks_1d(p.N), kThreads, 0, s>>>(p, rho, u, T, (S*)pop, status);
-    ++*launches;
+                        void* spare, void* qfield, double* partials, int* status, cudaStream_t s,
+                        long long* launches) {
+    const unsigned nb = blocks_1d(p.N);
+    init_kernel<<<nb, kThreads, 0, s>>>(p, rho, u, T, (S*)spare, status);
+    moments_kernel<false><<<nb, kThreads, 0, s>>>(p, (const S*)spare, (R*)qfield);
+    collide_kernel<false><<<nb, kThreads, 0, s>>>(p, (const S*)spare, (S*)pop, (const R*)qfield, partials, status);
+    *launches += 3;
     return cudaGetLastError();
 }
 
@@ -500,8 +515,8 @@ cudaError_t launch_fields(const KParams& p, const void* pop, double* rho, double
 cudaError_t launch_twopass(const KParams& p, const void* src, void* dst, void* qfield, double* partials,
                            int* nblocks, int* status, cudaStream_t s, long long* launches) {
     const unsigned nb = blocks_1d(p.N);
-    moments_kernel<<<nb, kThreads, 0, s>>>(p, (const S*)src, (R*)qfield);
-    collide_kernel<<<nb, kThreads, 0, s>>>(p, (const S*)src, (S*)dst, (const R*)qfield, partials, status);
+    moments_kernel<true><<<nb, kThreads, 0, s>>>(p, (const S*)src, (R*)qfield);
+    collide_kernel<true><<<nb, kThreads, 0, s>>>(p, (const S*)src, (S*)dst, (const R*)qfield, partials, status);
     *launches += 2;
     *nblocks = (int)nb;
     return cudaGetLastError();
