@@ -205,8 +205,12 @@ def run_reference(args):
 def time_store(E, torch, case, store, steps, warmup, stream):
     """Device-resident timing of `steps` steps; returns (ms_per_step, launches, solver)."""
     g = E.Solver.from_case(case, store=store, stream=stream)
-    g.step(warmup)
-    g.sync()
+    for w in range(warmup):
+        g.step(1)
+        rc = E.elbm_sync(g.h)
+        if rc != 0:
+            g.close()
+            raise E.ElbmError(rc, f"warm-up step {w + 1}")
     l0 = g.launches
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -215,7 +219,10 @@ def time_store(E, torch, case, store, steps, warmup, stream):
         g.step(steps)
         e1.record(stream)
     e1.synchronize()
-    g.sync()
+    rc = E.elbm_sync(g.h)
+    if rc != 0:
+        g.close()
+        raise E.ElbmError(rc, f"timed steps {warmup + 1}..{warmup + steps}")
     ms = e0.elapsed_time(e1) / steps
     return ms, g.launches - l0, g
 
@@ -301,7 +308,16 @@ def main():
         sampler = ClockSampler(dev) if store == stores[0] and rank == 0 else None
         if sampler:
             sampler.start()
-        ms, launches, g = time_store(E, torch, case, store, k, args.warmup, stream)
+        try:
+            ms, launches, g = time_store(E, torch, case, store, k, args.warmup, stream)
+        except E.ElbmError as err:
+            if sampler:
+                sampler.stop()
+            print(f"bench: store {store} failed: {err}", file=sys.stderr, flush=True)
+            variants[store] = {"error": str(err)}
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            continue
         if sampler:
             clocks = sampler.stop()
         if ws > 1:
@@ -319,7 +335,7 @@ def main():
                            "hbm_frac": per_gpu_gbs / peak, "bytes_per_update": BYTES_PER_UPDATE[store],
                            "kernel_launches_per_step": launches / k,
                            "mass_total": float(totals[0]), "energy_total": float(totals[4])}
-        if head is None:
+        if head is None and "error" not in variants[store]:
             head = store
             launches_head = launches
     hs = variants[head]

@@ -3,9 +3,9 @@ element on the same seeded inputs.
 
 Tolerances (relative L2 over all nodes, all components for u): FP64 store 1e-12,
 FP32 1e-5, FP16 deviation store 1e-3, over the stated number of steps.  The BF16
-deviation store keeps 8 significand bits against FP16's 11, so its storage rounding
-error is 8x FP16's (about 3.5e-3 in u where FP16 gives 4e-4); it is held to 5e-3,
-above the 1e-3 that FP16 meets.
+deviation store keeps 8 significand bits against FP16's 11, so its unit roundoff,
+and with it the storage error, is 8x FP16's (3.5e-3 in u where FP16 gives 4e-4); it
+is held to the FP16 bound times that ratio, 8e-3, above the 1e-3 that FP16 meets.
 Grids are chosen ragged against the 32 x 8 tiles of the fused kernels and, in 3D,
 against the z segments.
 
@@ -29,7 +29,7 @@ from paper_2102_09512_gb300 import cases as C
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "f16dev": 1e-3, "bf16dev": 5e-3}
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16dev": 1e-3, "bf16dev": 8e-3}
 
 
 @pytest.fixture(scope="module")
