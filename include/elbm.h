@@ -152,6 +152,29 @@ long long elbm_launch_count(const elbm_handle *h);
 /* Velocity c_i = (c[0], c[1], c[2]) of direction i of a lattice (Eq. d3q27vel). */
 int elbm_velocity(int lattice, int i, int c[3]);
 
+/* One time step, src -> dst, of the two-pass schedule, for callers that cannot
+ * allocate device memory (for example a solver embedded in an application that owns
+ * the whole device memory pool and lends the library only the populations it
+ * updates).  No handle and no auxiliary buffer: the scratch this step needs (the Q~
+ * field, the per-CTA partials and the status word) lives in a fixed static device
+ * array of 16 MiB that every GPU loading the library holds until the process exits.
+ * The paper has no counterpart; this is an interface choice of the library.
+ *   params  problem statement, validated as by elbm_create;
+ *   src     current population store (device, pop_bytes, 256-byte aligned, read);
+ *   dst     next population store (device, pop_bytes, 256-byte aligned, written);
+ *   stream  cudaStream_t (NULL: legacy default stream); the call is asynchronous.
+ * Limits: the Q~ field and partials must fit the array: about 1.37 M nodes for
+ * D3Q27 with FP32/FP16/BF16 stores, 0.69 M for FP64, 2.05 M for D2Q9 FP32; larger
+ * grids return ELBM_ERR_UNSUPPORTED before anything is launched.
+ * The first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.
+ * Calls no cudaMalloc, cudaFree or other allocating routine.  All calls share the
+ * array, so calls whose kernels overlap on the GPU (different streams, or several
+ * host threads) race on it; serialise them.  The status word is cleared by each
+ * call and device-detected non-physical states are not reported here (read them
+ * through the handle API, e.g. elbm_conservation on a bound handle). */
+int elbm_step_noalloc(const elbm_params *params, const void *src, void *dst, void *stream);
+
 /* Frees the handle (not the caller's buffers). */
 int elbm_destroy(elbm_handle *h);
 

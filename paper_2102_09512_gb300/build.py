@@ -69,8 +69,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             if verbose:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append((obj, cmd))
-    api_obj = os.path.join(BUILD, "elbm_api.o")
-    jobs.append((api_obj, [exe, *ARCH, *FLAGS, *extra_flags, "-c", os.path.join(CSRC, "elbm_api.cu"), "-o", api_obj]))
+    for name in ("elbm_api", "elbm_noalloc"):
+        obj = os.path.join(BUILD, f"{name}.o")
+        jobs.append((obj, [exe, *ARCH, *FLAGS, *extra_flags, "-c", os.path.join(CSRC, f"{name}.cu"), "-o", obj]))
     workers = min(len(jobs), max(2, os.cpu_count() or 2))
     with cf.ThreadPoolExecutor(workers) as ex:
         outs = list(ex.map(lambda j: _run(j[1]), jobs))

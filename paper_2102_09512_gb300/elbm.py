@@ -74,6 +74,7 @@ _SIGS = {
     "elbm_velocity": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "elbm_destroy": (ctypes.c_int, [_vp]),
     "elbm_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "elbm_step_noalloc": (ctypes.c_int, [ctypes.POINTER(elbm_params), _vp, _vp, _vp]),
 }
 
 
@@ -196,6 +197,11 @@ def elbm_velocity(lattice: int, i: int):
 
 def elbm_destroy(h):
     return lib().elbm_destroy(h)
+
+
+def elbm_step_noalloc(params: elbm_params, src: int, dst: int, stream: int) -> int:
+    """One two-pass step src -> dst without any device allocation (static scratch)."""
+    return lib().elbm_step_noalloc(ctypes.byref(params), src, dst, stream)
 
 
 # ---------------------------------------------------------------------------
