@@ -17,9 +17,10 @@
  *    rho[N], T[N], u[D*N] component-major (u_x block, then u_y, then u_z).
  *  - Memory: the caller owns every device buffer (two population stores and one
  *    auxiliary buffer, sizes from elbm_bytes_required) and the stream; the library
- *    owns only the handle.  Population layout (structure of arrays): plane k of
- *    N values for k = 0..2Q-1, f planes first, then g planes; direction
- *    i = (c_x+1) + 3(c_y+1) + 9(c_z+1).  Device pointers must be 256-byte aligned.
+ *    owns only the handle.  Population layout: Q planes of N elements, element
+ *    [i*N + n] holding the pair (f_i, g_i) of direction i = (c_x+1) + 3(c_y+1) +
+ *    9(c_z+1) at node n (both are pulled from the same source node, so one access
+ *    moves both).  Device pointers must be 256-byte aligned.
  *    The store holds the post-collision populations of the current time level
  *    (streaming is a pull at the start of the next step); their moments rho,
  *    rho u, rho E equal those of the post-stream state because the collision
@@ -68,8 +69,12 @@ typedef enum { ELBM_DERIV_UPWIND = 0, ELBM_DERIV_CENTRAL = 1 } elbm_deriv;
 
 /* Kernel schedule of one step. */
 typedef enum {
-    ELBM_KERNEL_FUSED = 0,    /* one kernel: halo-recomputed moments + collide + stream */
-    ELBM_KERNEL_TWOPASS = 1   /* moment/Q~ pass into the aux buffer, then collide+stream */
+    ELBM_KERNEL_FUSED = 0,        /* one kernel: halo-recomputed moments + collide + stream;
+                                     D3Q27 FP32/FP16/BF16 prefetch each plane into shared
+                                     memory (cp.async), FP64 uses the re-read form */
+    ELBM_KERNEL_TWOPASS = 1,      /* moment/Q~ pass into the aux buffer, then collide+stream */
+    ELBM_KERNEL_FUSED_REREAD = 2  /* one kernel, D3Q27 plane gathered twice (second from L2);
+                                     D2Q9 runs the fused kernel */
 } elbm_kernel;
 
 typedef struct {

@@ -263,6 +263,9 @@ int elbm_step(elbm_handle* h, int nsteps) {
         if (h->kernel == ELBM_KERNEL_TWOPASS)
             e = h->ops->step_twopass(h->kp, src, dst, h->auxp + h->aux.qfield, step_partials(h), &h->step_blocks,
                                      status_ptr(h), h->stream, &h->launches);
+        else if (h->kernel == ELBM_KERNEL_FUSED_REREAD)
+            e = h->ops->step_fused_reread(h->kp, src, dst, step_partials(h), &h->step_blocks, status_ptr(h),
+                                          h->stream, &h->launches);
         else
             e = h->ops->step_fused(h->kp, src, dst, step_partials(h), &h->step_blocks, status_ptr(h), h->stream,
                                    &h->launches);
@@ -308,7 +311,8 @@ int elbm_step_totals(elbm_handle* h, double out[5]) {
 }
 
 int elbm_set_kernel(elbm_handle* h, int kernel) {
-    if (!h || (kernel != ELBM_KERNEL_FUSED && kernel != ELBM_KERNEL_TWOPASS)) return ELBM_ERR_ARG;
+    if (!h || (kernel != ELBM_KERNEL_FUSED && kernel != ELBM_KERNEL_TWOPASS && kernel != ELBM_KERNEL_FUSED_REREAD))
+        return ELBM_ERR_ARG;
     h->kernel = kernel;
     return ELBM_OK;
 }

@@ -36,6 +36,8 @@ struct Ops {
                                 long long* launches);
     cudaError_t (*step_fused)(const KParams& p, const void* src, void* dst, double* partials,
                               int* nblocks, int* status, cudaStream_t s, long long* launches);
+    cudaError_t (*step_fused_reread)(const KParams& p, const void* src, void* dst, double* partials,
+                                     int* nblocks, int* status, cudaStream_t s, long long* launches);
     cudaError_t (*conservation)(const KParams& p, const void* pop, double* partials, int* nblocks,
                                 cudaStream_t s, long long* launches);
 };

@@ -2,17 +2,23 @@
 // ELBM_D (2 or 3) and ELBM_ST (elbm::StoreKind).  Built once per combination so
 // the eight variants compile in parallel.
 //
-//   init_kernel        f = f^eq, g = g^eq of (rho, u, T)              (Eqs. 27eq, geq_i)
-//   fields_kernel      rho, u, T of the current populations           (Eqs. density..E)
-//   moments_kernel     two-pass schedule, pass 1: Q~_aaa field        (Eq. anomalya)
-//   collide_kernel     two-pass schedule, pass 2: pull, collide, store (Eqs. fLBGK, gLBGK)
-//   fused2d_kernel     D2Q9 one-kernel step: tile + halo moments in shared memory
-//   fused3d_kernel     D3Q27 one-kernel step: xy tile + halo, marching along z
-//   totals_kernel      FP64 totals of the current state (per-CTA partials)
+//   init_kernel          f = f^eq, g = g^eq of (rho, u, T)              (Eqs. 27eq, geq_i)
+//   fields_kernel        rho, u, T of the current populations           (Eqs. density..E)
+//   totals_kernel        FP64 totals of the current state (per-CTA partials)
+//   moments_kernel       two-pass schedule, pass 1: Q~_aaa field        (Eq. anomalya)
+//   collide_kernel       two-pass schedule, pass 2: pull, collide, store (Eqs. fLBGK, gLBGK)
+//   fused2d_kernel       D2Q9 one-kernel step: tile + halo moments in shared memory
+//   fused3d_kernel       D3Q27 one-kernel step: xy tile + halo marching along z, the pulled
+//                        populations of each plane prefetched into shared memory with
+//                        cp.async one plane ahead
+//   fused3d_reread_kernel  D3Q27 one-kernel step without the shared-memory plane buffers:
+//                        the populations of a plane are gathered twice (moments of the
+//                        next plane, then the collision), the second time from L2
 //
-// Streaming is "pull": the value of direction i at node x is read from x - c_i of
-// the source store and the post-collision value is written at x in the destination
-// store (ping-pong), so every store is coalesced and no two threads write one slot.
+// Layout: element [i * N + n] holds the pair (f_i, g_i) of direction i at node n.
+// Streaming is "pull": the pair of direction i at node x is read from x - c_i of the
+// source store and the post-collision pair is written at x in the destination store
+// (ping-pong), so every store is coalesced and no two threads write one element.
 #include <cuda_runtime.h>
 
 #include "elbm_internal.h"
@@ -31,7 +37,7 @@ namespace {
 constexpr int kD = ELBM_D;
 constexpr int kST = ELBM_ST;
 using Cd = Codec<kST>;
-using S = typename Cd::S;
+using P = typename Cd::P;
 using R = typename Cd::R;
 constexpr int Q = Lat<kD>::Q;
 
@@ -42,11 +48,11 @@ __device__ __forceinline__ long long node_index(const KParams& p, int x, int y, 
     return (long long)x + (long long)p.nx * ((long long)y + (long long)p.ny * (long long)z);
 }
 
-// Pull-gather of the 2Q populations arriving at node (x, y, z): direction i is read
-// at (x - c_x, y - c_y, z - c_z) with ghost nodes resolved by map_axis.
+// Source nodes of the pull at node (x, y, z): direction i = a + 3b + 9c is read at
+// (xs[a], ys[b], zs[c]) = (x - c_x, y - c_y, z - c_z) with ghosts resolved by map_axis.
 struct PullRows {
-    long long row[3][3];   // node index of (0, y - c_y, z - c_z) for b = c_y+1, c = c_z+1
-    int xs[3];             // x - c_x for a = c_x+1
+    long long row[3][3];   // node index of (0, ys[b], zs[c])
+    int xs[3];
 };
 
 // With PULL = false every direction is read at the node itself (no streaming);
@@ -69,26 +75,29 @@ __device__ __forceinline__ void pull_rows(const KParams& p, int x, int y, int z,
             r.row[b][c] = (long long)p.nx * ((long long)ys[b] + (long long)p.ny * (long long)zs[c]);
 }
 
-__device__ __forceinline__ void gather(const KParams& p, const S* __restrict__ src, const PullRows& r,
-                                       R* f, R* g) {
-    const size_t N = (size_t)p.N;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int a = i % 3, b = (i / 3) % 3, c = (kD == 3) ? i / 9 : 1;
-        const size_t n = (size_t)(r.row[b][c] + r.xs[a]);
-        f[i] = Cd::load(src, (size_t)i * N + n, p.rest32[i]);
-        g[i] = Cd::load(src, (size_t)(Q + i) * N + n, p.rest32[Q + i]);
-    }
+__device__ __forceinline__ size_t src_elem(const KParams& p, const PullRows& r, int i) {
+    const int a = i % 3, b = (i / 3) % 3, c = (kD == 3) ? i / 9 : 1;
+    return (size_t)i * (size_t)p.N + (size_t)(r.row[b][c] + r.xs[a]);
 }
 
-__device__ __forceinline__ void store_node(const KParams& p, S* __restrict__ dst, long long n,
-                                           const R* f, const R* g) {
-    const size_t N = (size_t)p.N;
+__device__ __forceinline__ void gather(const KParams& p, const P* __restrict__ src, const PullRows& r,
+                                       R* f, R* g) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        dst[(size_t)i * N + (size_t)n] = Cd::enc(f[i], p.rest32[i]);
-        dst[(size_t)(Q + i) * N + (size_t)n] = Cd::enc(g[i], p.rest32[Q + i]);
-    }
+    for (int i = 0; i < Q; ++i) Cd::dec(src[src_elem(p, r, i)], p.rest32[i], p.rest32[Q + i], f[i], g[i]);
+}
+
+__device__ __forceinline__ void load_local(const KParams& p, const P* __restrict__ pop, long long n, R* f,
+                                           R* g) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        Cd::dec(pop[(size_t)i * (size_t)p.N + (size_t)n], p.rest32[i], p.rest32[Q + i], f[i], g[i]);
+}
+
+__device__ __forceinline__ void store_node(const KParams& p, P* __restrict__ dst, long long n, const R* f,
+                                           const R* g) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        dst[(size_t)i * (size_t)p.N + (size_t)n] = Cd::enc(f[i], g[i], p.rest32[i], p.rest32[Q + i]);
 }
 
 // Totals of one node: rho, rho u_x, rho u_y, rho u_z, rho E.
@@ -100,9 +109,8 @@ __device__ __forceinline__ void node_totals(const Moments<R>& m, R rE, R v[5]) {
     v[4] = rE;
 }
 
-template <typename T>
-__device__ __forceinline__ T sum_g(const T* g) {
-    T s = 0;
+__device__ __forceinline__ R sum_g(const R* g) {
+    R s = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) s += g[i];
     return s;
@@ -158,12 +166,24 @@ __device__ __forceinline__ void flag_if(bool bad, int* __restrict__ status) {
     if (any && (threadIdx.x & 31) == 0 && status) atomicOr(status, 1);
 }
 
+// Asynchronous global -> shared copy of one pair (cp.async, bypasses registers).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // initial state and field extraction
 // ---------------------------------------------------------------------------
 __global__ void init_kernel(const __grid_constant__ KParams p, const double* __restrict__ rho,
                             const double* __restrict__ u, const double* __restrict__ T,
-                            S* __restrict__ pop, int* __restrict__ status) {
+                            P* __restrict__ pop, int* __restrict__ status) {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool bad = false;
     if (n < p.N) {
@@ -178,19 +198,14 @@ __global__ void init_kernel(const __grid_constant__ KParams p, const double* __r
     flag_if(bad, status);
 }
 
-__global__ void fields_kernel(const __grid_constant__ KParams p, const S* __restrict__ pop,
+__global__ void fields_kernel(const __grid_constant__ KParams p, const P* __restrict__ pop,
                               double* __restrict__ rho, double* __restrict__ u,
                               double* __restrict__ T, int* __restrict__ status) {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool bad = false;
     if (n < p.N) {
         R f[Q], g[Q];
-        const size_t N = (size_t)p.N;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            f[i] = Cd::load(pop, (size_t)i * N + n, p.rest32[i]);
-            g[i] = Cd::load(pop, (size_t)(Q + i) * N + n, p.rest32[Q + i]);
-        }
+        load_local(p, pop, n, f, g);
         Moments<R> m;
         node_moments<kD, R, false>(f, g, R(p.gm1), m);
         rho[n] = m.rho;
@@ -204,18 +219,13 @@ __global__ void fields_kernel(const __grid_constant__ KParams p, const S* __rest
 }
 
 // FP64 totals of the current state: one partial per CTA (grid-stride loop).
-__global__ void totals_kernel(const __grid_constant__ KParams p, const S* __restrict__ pop,
+__global__ void totals_kernel(const __grid_constant__ KParams p, const P* __restrict__ pop,
                               double* __restrict__ partials) {
     double s[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0};
-    const size_t N = (size_t)p.N;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < p.N;
          n += (long long)gridDim.x * blockDim.x) {
         R f[Q], g[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            f[i] = Cd::load(pop, (size_t)i * N + n, p.rest32[i]);
-            g[i] = Cd::load(pop, (size_t)(Q + i) * N + n, p.rest32[Q + i]);
-        }
+        load_local(p, pop, n, f, g);
         double v[5] = {0, 0, 0, 0, 0};
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -243,7 +253,7 @@ __global__ void totals_kernel(const __grid_constant__ KParams p, const S* __rest
 // ---------------------------------------------------------------------------
 // Pass 1: Q~_aaa at every node from the pulled (post-stream) populations.
 template <bool PULL>
-__global__ void moments_kernel(const __grid_constant__ KParams p, const S* __restrict__ src,
+__global__ void moments_kernel(const __grid_constant__ KParams p, const P* __restrict__ src,
                                R* __restrict__ qf) {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
@@ -263,8 +273,8 @@ __global__ void moments_kernel(const __grid_constant__ KParams p, const S* __res
 
 // Pass 2: pull, moments, derivative of Q~ from the field, collide, store.
 template <bool PULL>
-__global__ void collide_kernel(const __grid_constant__ KParams p, const S* __restrict__ src,
-                               S* __restrict__ dst, const R* __restrict__ qf,
+__global__ void collide_kernel(const __grid_constant__ KParams p, const P* __restrict__ src,
+                               P* __restrict__ dst, const R* __restrict__ qf,
                                double* __restrict__ partials, int* __restrict__ status) {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double tot[5] = {0, 0, 0, 0, 0};
@@ -304,40 +314,35 @@ __global__ void collide_kernel(const __grid_constant__ KParams p, const S* __res
 }
 
 // ---------------------------------------------------------------------------
-// fused schedule
+// fused schedules
 // ---------------------------------------------------------------------------
 constexpr int TX = 32;
 
-// Moments of the node (hx, hy, z) (already mapped), returning one anomaly component.
-__device__ __forceinline__ R halo_anomaly(const KParams& p, const S* __restrict__ src, int hx, int hy,
-                                          int z, int axis) {
-    PullRows r;
-    pull_rows(p, hx, hy, z, r);
-    R f[Q], g[Q];
-    gather(p, src, r, f, g);
-    Moments<R> m;
-    node_moments<kD, R, false>(f, g, R(p.gm1), m);
-    return anomaly(m.rho, axis == 0 ? m.ux : (axis == 1 ? m.uy : m.uz), m.T);
-}
-
-// Halo ring of an xy tile: 2*TX row nodes (need Q~_yyy) and 2*TY column nodes (need
-// Q~_xxx).  Corner nodes are never needed: the stencil uses axis neighbours only.
+// Halo ring of a TX x TY tile: 2*TX row nodes (they need Q~_yyy) and 2*TY column
+// nodes (Q~_xxx).  Corners are never needed: the stencil uses axis neighbours only.
+// Halo node h: [0,TX) row below, [TX,2TX) row above, then the left and right columns.
+// Returns false for slots outside a ragged tile; (hx, hy) are mapped by the BCs and
+// (sx, sy) is where its Q~ goes: qy[sy][sx] for rows, qx[sy][sx] for columns.
 template <int TY>
-__device__ __forceinline__ void tile_halo(const KParams& p, const S* __restrict__ src, int z, int x0,
-                                          int y0, int xl, int yl, R (*qx)[TX + 2], R (*qy)[TX]) {
-    const int h = threadIdx.x + TX * threadIdx.y;
+__device__ __forceinline__ bool halo_node(const KParams& p, int h, int x0, int y0, int xl, int yl, int& hx,
+                                          int& hy, int& sx, int& sy, int& axis) {
     if (h < TX) {
-        if (h <= xl) qy[0][h] = halo_anomaly(p, src, x0 + h, map_axis(y0 - 1, p.ny, p.per_y), z, 1);
-    } else if (h < 2 * TX) {
-        const int hx = h - TX;
-        if (hx <= xl) qy[yl + 2][hx] = halo_anomaly(p, src, x0 + hx, map_axis(y0 + yl + 1, p.ny, p.per_y), z, 1);
-    } else if (h < 2 * TX + TY) {
-        const int hy = h - 2 * TX;
-        if (hy <= yl) qx[hy][0] = halo_anomaly(p, src, map_axis(x0 - 1, p.nx, p.per_x), y0 + hy, z, 0);
-    } else if (h < 2 * TX + 2 * TY) {
-        const int hy = h - 2 * TX - TY;
-        if (hy <= yl) qx[hy][xl + 2] = halo_anomaly(p, src, map_axis(x0 + xl + 1, p.nx, p.per_x), y0 + hy, z, 0);
+        hx = x0 + h; hy = map_axis(y0 - 1, p.ny, p.per_y); sx = h; sy = 0; axis = 1;
+        return h <= xl;
     }
+    if (h < 2 * TX) {
+        const int k = h - TX;
+        hx = x0 + k; hy = map_axis(y0 + yl + 1, p.ny, p.per_y); sx = k; sy = yl + 2; axis = 1;
+        return k <= xl;
+    }
+    if (h < 2 * TX + TY) {
+        const int k = h - 2 * TX;
+        hx = map_axis(x0 - 1, p.nx, p.per_x); hy = y0 + k; sx = 0; sy = k; axis = 0;
+        return k <= yl;
+    }
+    const int k = h - 2 * TX - TY;
+    hx = map_axis(x0 + xl + 1, p.nx, p.per_x); hy = y0 + k; sx = xl + 2; sy = k; axis = 0;
+    return k <= yl;
 }
 
 // D2Q9: one thread per node of a TX x TY tile.  Phase 1 pulls the populations into
@@ -345,7 +350,7 @@ __device__ __forceinline__ void tile_halo(const KParams& p, const S* __restrict_
 // collides and stores.  One launch per step, no intermediate field in HBM.
 template <int TY>
 __global__ void __launch_bounds__(TX * TY)
-fused2d_kernel(const __grid_constant__ KParams p, const S* __restrict__ src, S* __restrict__ dst,
+fused2d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* __restrict__ dst,
                double* __restrict__ partials, int* __restrict__ status) {
     __shared__ R qx[TY][TX + 2];
     __shared__ R qy[TY + 2][TX];
@@ -365,7 +370,20 @@ fused2d_kernel(const __grid_constant__ KParams p, const S* __restrict__ src, S* 
         qx[ty][tx + 1] = anomaly(m.rho, m.ux, m.T);
         qy[ty + 1][tx] = anomaly(m.rho, m.uy, m.T);
     }
-    tile_halo<TY>(p, src, 0, x0, y0, xl, yl, qx, qy);
+    {
+        int hx, hy, sx, sy, axis;
+        const int h = tx + TX * ty;
+        if (h < 2 * TX + 2 * TY && halo_node<TY>(p, h, x0, y0, xl, yl, hx, hy, sx, sy, axis)) {
+            PullRows r;
+            pull_rows(p, hx, hy, 0, r);
+            R hf[Q], hg[Q];
+            gather(p, src, r, hf, hg);
+            Moments<R> hm;
+            node_moments<kD, R, false>(hf, hg, R(p.gm1), hm);
+            if (axis == 1) qy[sy][sx] = anomaly(hm.rho, hm.uy, hm.T);
+            else qx[sy][sx] = anomaly(hm.rho, hm.ux, hm.T);
+        }
+    }
     __syncthreads();
 
     double tot[5] = {0, 0, 0, 0, 0};
@@ -385,26 +403,194 @@ fused2d_kernel(const __grid_constant__ KParams p, const S* __restrict__ src, S* 
     block_sum5(tot, partials + 5 * (blockIdx.x + gridDim.x * blockIdx.y));
 }
 
-// D3Q27: a CTA owns a TX x TY column of nodes and marches along z over a segment of
-// p.tz planes.  For plane z it needs Q~ at z-1, z, z+1 (z-components, kept in
-// registers as a rolling window) and at the x/y neighbours in plane z (shared
-// memory, halo ring recomputed from the pulled populations).  Per plane: moments
-// of plane z+1 (tile + halo) into buffer b^1, barrier, collide plane z from buffer
-// b.  The populations of plane z are pulled again for the collision; they were
-// read one plane earlier by this CTA and its neighbours, so the re-read is an L2
-// hit and HBM sees each population about once per step.
-template <int TY>
-__global__ void __launch_bounds__(TX * TY, 2)
-fused3d_kernel(const __grid_constant__ KParams p, const S* __restrict__ src, S* __restrict__ dst,
+// Q~_zzz of the node (x, y, z) by a direct gather (used once per z segment).
+__device__ __forceinline__ R direct_anomaly_z(const KParams& p, const P* __restrict__ src, int x, int y, int z) {
+    PullRows r;
+    pull_rows(p, x, y, z, r);
+    R f[Q], g[Q];
+    gather(p, src, r, f, g);
+    Moments<R> m;
+    node_moments<kD, R, false>(f, g, R(p.gm1), m);
+    return anomaly(m.rho, m.uz, m.T);
+}
+
+// D3Q27, pipelined.  A CTA owns a TX x TY column of nodes and marches along z over a
+// segment of p.tz planes.  For every plane q it needs the pulled pairs of its TX*TY
+// nodes and of the 2TX+2TY halo nodes; these are copied with cp.async into one of
+// NB shared-memory plane buffers, laid out [direction][slot] so that each thread
+// reads its own slot (conflict-free).  Per plane z:
+//   [A] wait for plane z+1, barrier; (NB = 3: prefetch plane z+2 into the buffer of
+//       plane z-1);
+//   moments of plane z+1 (tile and halo) -> Q~ in shared memory, moments kept in
+//       registers for the next iteration;
+//   [B] barrier; read the pairs of plane z from shared memory;
+//   (NB = 2: [C] barrier, prefetch plane z+2 into the buffer of plane z);
+//   collide plane z (moments from the previous iteration, Q~ neighbours from shared
+//       memory and the rolling Q~_zzz registers) and store.
+// Every population leaves HBM once per step; the collision overlaps the prefetch.
+template <int TY, int NB>
+struct Pipe {
+    static constexpr int NT = TX * TY;
+    static constexpr int NH = 2 * TX + 2 * TY;
+    static constexpr int NS = NT + NH;
+    static constexpr size_t buf_bytes = (size_t)NB * Q * NS * sizeof(P);
+    static constexpr size_t q_bytes = (size_t)2 * (TY * (TX + 2) + (TY + 2) * TX) * sizeof(R);
+    static constexpr size_t smem_bytes = buf_bytes + q_bytes;
+};
+
+template <int TY, int NB, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB)
+fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* __restrict__ dst,
                double* __restrict__ partials, int* __restrict__ status) {
-    __shared__ R qx[2][TY][TX + 2];
-    __shared__ R qy[2][TY + 2][TX];
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    using PP = Pipe<TY, NB>;
+    constexpr int NT = PP::NT, NH = PP::NH, NS = PP::NS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    P* buf = reinterpret_cast<P*>(smem_raw);                       // [NB][Q][NS]
+    R* qxs = reinterpret_cast<R*>(smem_raw + PP::buf_bytes);       // [2][TY][TX+2]
+    R* qys = qxs + 2 * TY * (TX + 2);                              // [2][TY+2][TX]
+    auto QX = [&](int b, int row, int col) -> R& { return qxs[(b * TY + row) * (TX + 2) + col]; };
+    auto QY = [&](int b, int row, int col) -> R& { return qys[(b * (TY + 2) + row) * TX + col]; };
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int zb = blockIdx.z * p.tz, ze = min(zb + p.tz, p.nz);
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < p.nx && y < p.ny;
     const int xl = min(x0 + TX, p.nx) - 1 - x0, yl = min(y0 + TY, p.ny) - 1 - y0;
+
+    // this thread's halo node (if any) is fixed for the whole segment
+    int hx = 0, hy = 0, hsx = 0, hsy = 0, haxis = 0;
+    const bool has_halo = tid < NH && halo_node<TY>(p, tid, x0, y0, xl, yl, hx, hy, hsx, hsy, haxis);
+
+    // copies of plane q (already mapped) into buffer sb
+    auto issue_plane = [&](int q, int sb, bool with_halo) {
+        P* bb = buf + (size_t)sb * Q * NS;
+        if (active) {
+            PullRows r;
+            pull_rows(p, x, y, q, r);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) cp_async<sizeof(P)>(bb + i * NS + tid, src + src_elem(p, r, i));
+        }
+        if (with_halo && has_halo) {
+            PullRows r;
+            pull_rows(p, hx, hy, q, r);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) cp_async<sizeof(P)>(bb + i * NS + NT + tid, src + src_elem(p, r, i));
+        }
+        cp_async_commit();
+    };
+    // moments of the node in slot `slot` of buffer sb; returns rho E
+    auto slot_moments = [&](int sb, int slot, Moments<R>& m) -> R {
+        const P* bb = buf + (size_t)sb * Q * NS + slot;
+        R f[Q], g[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], p.rest32[i], p.rest32[Q + i], f[i], g[i]);
+        node_moments<kD, R, true>(f, g, R(p.gm1), m);
+        return sum_g(g);
+    };
+
+    Acc5 acc;
+    acc.zero();
+    bool bad = false;
+
+    // prologue: Q~_zzz below the segment, planes zb and zb+1 in flight, moments of zb
+    R qz_prev = R(0), qz_cur = R(0), qz_next = R(0);
+    if (active) qz_prev = direct_anomaly_z(p, src, x, y, map_axis(zb - 1, p.nz, p.per_z));
+    issue_plane(zb, 0, true);
+    issue_plane(map_axis(zb + 1, p.nz, p.per_z), 1 % NB, zb + 1 < ze);
+    Moments<R> m_cur, m_next;
+    R rE_cur = R(0), rE_next = R(0);
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();
+    if (active) {
+        rE_cur = slot_moments(0, tid, m_cur);
+        QX(0, ty, tx + 1) = anomaly(m_cur.rho, m_cur.ux, m_cur.T);
+        QY(0, ty + 1, tx) = anomaly(m_cur.rho, m_cur.uy, m_cur.T);
+        qz_cur = anomaly(m_cur.rho, m_cur.uz, m_cur.T);
+    }
+    if (has_halo) {
+        Moments<R> hm;
+        slot_moments(0, NT + tid, hm);
+        if (haxis == 1) QY(0, hsy, hsx) = anomaly(hm.rho, hm.uy, hm.T);
+        else QX(0, hsy, hsx) = anomaly(hm.rho, hm.ux, hm.T);
+    }
+
+    for (int z = zb; z < ze; ++z) {
+        const int k = z - zb;
+        const int bq = k & 1;               // Q~ buffer of plane z
+        const int sz = k % NB;              // population buffer of plane z
+        const int sn = (k + 1) % NB;        // ... of plane z+1
+        const bool last = (z + 1 == ze);
+        cp_async_wait_all();
+        __syncthreads();                                                     // [A]
+        if (NB == 3 && z + 2 <= ze) issue_plane(map_axis(z + 2, p.nz, p.per_z), (k + 2) % NB, z + 2 < ze);
+
+        if (active) {
+            rE_next = slot_moments(sn, tid, m_next);
+            qz_next = anomaly(m_next.rho, m_next.uz, m_next.T);
+            if (!last) {
+                QX(bq ^ 1, ty, tx + 1) = anomaly(m_next.rho, m_next.ux, m_next.T);
+                QY(bq ^ 1, ty + 1, tx) = anomaly(m_next.rho, m_next.uy, m_next.T);
+            }
+        }
+        if (!last && has_halo) {
+            Moments<R> hm;
+            slot_moments(sn, NT + tid, hm);
+            if (haxis == 1) QY(bq ^ 1, hsy, hsx) = anomaly(hm.rho, hm.uy, hm.T);
+            else QX(bq ^ 1, hsy, hsx) = anomaly(hm.rho, hm.ux, hm.T);
+        }
+        __syncthreads();                                                     // [B]
+
+        R f[Q], g[Q];
+        if (active) {
+            const P* bb = buf + (size_t)sz * Q * NS + tid;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], p.rest32[i], p.rest32[Q + i], f[i], g[i]);
+        }
+        if (NB == 2) {
+            __syncthreads();                                                 // [C]
+            if (z + 2 <= ze) issue_plane(map_axis(z + 2, p.nz, p.per_z), sz, z + 2 < ze);
+        }
+        if (active) {
+            bad |= nonphysical(m_cur);
+            const R Dx = dQ(p.deriv, m_cur.ux, QX(bq, ty, tx), QX(bq, ty, tx + 1), QX(bq, ty, tx + 2));
+            const R Dy = dQ(p.deriv, m_cur.uy, QY(bq, ty, tx), QY(bq, ty + 1, tx), QY(bq, ty + 2, tx));
+            const R Dz = dQ(p.deriv, m_cur.uz, qz_prev, qz_cur, qz_next);
+            R v[5];
+            node_totals(m_cur, rE_cur, v);
+            acc.add(v);
+            collide<kD, R>(f, g, m_cur, Dx, Dy, Dz, p);
+            store_node(p, dst, node_index(p, x, y, z), f, g);
+        }
+        m_cur = m_next;
+        rE_cur = rE_next;
+        qz_prev = qz_cur;
+        qz_cur = qz_next;
+    }
+    cp_async_wait_all();
+    flag_if(bad, status);
+    double tot[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) tot[k] = (double)acc.s[k] - (double)acc.c[k];
+    block_sum5(tot, partials + 5 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
+}
+
+// D3Q27 without plane buffers: for plane z it computes Q~ of plane z+1 (tile + halo)
+// from a first gather, then gathers plane z again (an L2 hit) to collide it.
+template <int TY>
+__global__ void __launch_bounds__(TX * TY, 2)
+fused3d_reread_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* __restrict__ dst,
+                      double* __restrict__ partials, int* __restrict__ status) {
+    __shared__ R qx[2][TY][TX + 2];
+    __shared__ R qy[2][TY + 2][TX];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int zb = blockIdx.z * p.tz, ze = min(zb + p.tz, p.nz);
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < p.nx && y < p.ny;
+    const int xl = min(x0 + TX, p.nx) - 1 - x0, yl = min(y0 + TY, p.ny) - 1 - y0;
+    int hx = 0, hy = 0, hsx = 0, hsy = 0, haxis = 0;
+    const bool has_halo = tid < 2 * TX + 2 * TY && halo_node<TY>(p, tid, x0, y0, xl, yl, hx, hy, hsx, hsy, haxis);
 
     // Q~ of the tile and its halo in plane z -> buffer b; returns Q~_zzz of (x, y, z)
     auto plane_moments = [&](int z, int b, bool with_xy) -> R {
@@ -422,7 +608,16 @@ fused3d_kernel(const __grid_constant__ KParams p, const S* __restrict__ src, S* 
             }
             qz = anomaly(m.rho, m.uz, m.T);
         }
-        if (with_xy) tile_halo<TY>(p, src, z, x0, y0, xl, yl, qx[b], qy[b]);
+        if (with_xy && has_halo) {
+            PullRows r;
+            pull_rows(p, hx, hy, z, r);
+            R f[Q], g[Q];
+            gather(p, src, r, f, g);
+            Moments<R> m;
+            node_moments<kD, R, false>(f, g, R(p.gm1), m);
+            if (haxis == 1) qy[b][hsy][hsx] = anomaly(m.rho, m.uy, m.T);
+            else qx[b][hsy][hsx] = anomaly(m.rho, m.ux, m.T);
+        }
         return qz;
     };
 
@@ -469,8 +664,15 @@ fused3d_kernel(const __grid_constant__ KParams p, const S* __restrict__ src, S* 
 // ---------------------------------------------------------------------------
 constexpr int kThreads = 256;
 constexpr int kTY2 = 8;                  // D2Q9 fused tile 32 x 8
-constexpr int kTY3 = 8;                  // D3Q27 fused tile 32 x 8
+constexpr int kTY3 = 8;                  // D3Q27 fused tiles 32 x 8
 constexpr int kTotalsBlocks = 2 * 152;   // totals_kernel grid (grid-stride)
+// Pipelined D3Q27 kernel per store: FP32 keeps three plane buffers (218 KB, one CTA
+// per SM, up to 255 registers); FP16/BF16 pairs are half the size, so two buffers
+// and two CTAs per SM; FP64 uses the re-read kernel (its plane buffers would not fit).
+constexpr bool kPipe = (kST != ST_F64);
+constexpr int kNB = (kST == ST_F32) ? 3 : 2;
+constexpr int kMinB = (kST == ST_F32) ? 1 : 2;
+using PipeCfg = Pipe<kTY3, kNB>;
 
 inline unsigned blocks_1d(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
@@ -488,26 +690,26 @@ int max_blocks(const KParams& p) {
     return (int)m;
 }
 
-// The stored state is post-collision: after step n the store holds C(X_n), where
-// X_n is the post-stream state of the method and C the collision, and a step is
-// pull (X_{n+1} = S(C(X_n))) followed by collide.  Initialisation therefore writes
-// X_0 = (f^eq, g^eq) into the spare store and collides it in place of streaming.
-// Moments of C(X_n) equal those of X_n (the collision conserves them), so field
-// extraction and totals read each node's own values.
 cudaError_t launch_init(const KParams& p, const double* rho, const double* u, const double* T, void* pop,
                         void* spare, void* qfield, double* partials, int* status, cudaStream_t s,
                         long long* launches) {
+    // The stored state is post-collision: after step n the store holds C(X_n), where
+    // X_n is the post-stream state of the method and C the collision, and a step is
+    // pull (X_{n+1} = S(C(X_n))) followed by collide.  Initialisation therefore writes
+    // X_0 = (f^eq, g^eq) into the spare store and collides it in place of streaming.
+    // Moments of C(X_n) equal those of X_n (the collision conserves them), so field
+    // extraction and totals read each node's own values.
     const unsigned nb = blocks_1d(p.N);
-    init_kernel<<<nb, kThreads, 0, s>>>(p, rho, u, T, (S*)spare, status);
-    moments_kernel<false><<<nb, kThreads, 0, s>>>(p, (const S*)spare, (R*)qfield);
-    collide_kernel<false><<<nb, kThreads, 0, s>>>(p, (const S*)spare, (S*)pop, (const R*)qfield, partials, status);
+    init_kernel<<<nb, kThreads, 0, s>>>(p, rho, u, T, (P*)spare, status);
+    moments_kernel<false><<<nb, kThreads, 0, s>>>(p, (const P*)spare, (R*)qfield);
+    collide_kernel<false><<<nb, kThreads, 0, s>>>(p, (const P*)spare, (P*)pop, (const R*)qfield, partials, status);
     *launches += 3;
     return cudaGetLastError();
 }
 
 cudaError_t launch_fields(const KParams& p, const void* pop, double* rho, double* u, double* T, int* status,
                           cudaStream_t s, long long* launches) {
-    fields_kernel<<<blocks_1d(p.N), kThreads, 0, s>>>(p, (const S*)pop, rho, u, T, status);
+    fields_kernel<<<blocks_1d(p.N), kThreads, 0, s>>>(p, (const P*)pop, rho, u, T, status);
     ++*launches;
     return cudaGetLastError();
 }
@@ -515,36 +717,63 @@ cudaError_t launch_fields(const KParams& p, const void* pop, double* rho, double
 cudaError_t launch_twopass(const KParams& p, const void* src, void* dst, void* qfield, double* partials,
                            int* nblocks, int* status, cudaStream_t s, long long* launches) {
     const unsigned nb = blocks_1d(p.N);
-    moments_kernel<true><<<nb, kThreads, 0, s>>>(p, (const S*)src, (R*)qfield);
-    collide_kernel<true><<<nb, kThreads, 0, s>>>(p, (const S*)src, (S*)dst, (const R*)qfield, partials, status);
+    moments_kernel<true><<<nb, kThreads, 0, s>>>(p, (const P*)src, (R*)qfield);
+    collide_kernel<true><<<nb, kThreads, 0, s>>>(p, (const P*)src, (P*)dst, (const R*)qfield, partials, status);
     *launches += 2;
     *nblocks = (int)nb;
     return cudaGetLastError();
 }
 
 cudaError_t launch_fused(const KParams& p, const void* src, void* dst, double* partials, int* nblocks,
-                         int* status, cudaStream_t s, long long* launches) {
+                         int* status, cudaStream_t s, long long* launches, bool reread) {
     const dim3 grid = fused_grid(p);
     if constexpr (kD == 2) {
-        fused2d_kernel<kTY2><<<grid, dim3(TX, kTY2), 0, s>>>(p, (const S*)src, (S*)dst, partials, status);
+        fused2d_kernel<kTY2><<<grid, dim3(TX, kTY2), 0, s>>>(p, (const P*)src, (P*)dst, partials, status);
     } else {
-        fused3d_kernel<kTY3><<<grid, dim3(TX, kTY3), 0, s>>>(p, (const S*)src, (S*)dst, partials, status);
+        bool launched = false;
+        if constexpr (kPipe) {
+            if (!reread) {
+                auto kern = fused3d_kernel<kTY3, kNB, kMinB>;
+                // the dynamic shared-memory limit is a per-function attribute; setting it
+                // again is cheap and keeps this correct for every device of the process
+                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)PipeCfg::smem_bytes);
+                if (e != cudaSuccess) return e;
+                kern<<<grid, dim3(TX, kTY3), PipeCfg::smem_bytes, s>>>(p, (const P*)src, (P*)dst, partials,
+                                                                       status);
+                launched = true;
+            }
+        }
+        if (!launched)
+            fused3d_reread_kernel<kTY3><<<grid, dim3(TX, kTY3), 0, s>>>(p, (const P*)src, (P*)dst, partials,
+                                                                         status);
     }
     ++*launches;
     *nblocks = (int)(grid.x * grid.y * grid.z);
     return cudaGetLastError();
 }
 
+cudaError_t launch_fused_default(const KParams& p, const void* src, void* dst, double* partials, int* nblocks,
+                                 int* status, cudaStream_t s, long long* launches) {
+    return launch_fused(p, src, dst, partials, nblocks, status, s, launches, false);
+}
+
+cudaError_t launch_fused_reread(const KParams& p, const void* src, void* dst, double* partials, int* nblocks,
+                                int* status, cudaStream_t s, long long* launches) {
+    return launch_fused(p, src, dst, partials, nblocks, status, s, launches, true);
+}
+
 cudaError_t launch_totals(const KParams& p, const void* pop, double* partials, int* nblocks, cudaStream_t s,
                           long long* launches) {
-    totals_kernel<<<kTotalsBlocks, kThreads, 0, s>>>(p, (const S*)pop, partials);
+    totals_kernel<<<kTotalsBlocks, kThreads, 0, s>>>(p, (const P*)pop, partials);
     ++*launches;
     *nblocks = kTotalsBlocks;
     return cudaGetLastError();
 }
 
-const Ops kOps = {kD, kST, sizeof(S), sizeof(R), max_blocks, launch_init, launch_fields,
-                  launch_twopass, launch_fused, launch_totals};
+const Ops kOps = {kD,          kST,           sizeof(P) / 2,  sizeof(R),            max_blocks,
+                  launch_init, launch_fields, launch_twopass, launch_fused_default, launch_fused_reread,
+                  launch_totals};
 
 }  // namespace
 

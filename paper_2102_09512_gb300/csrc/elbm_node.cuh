@@ -35,37 +35,46 @@ struct KParams {
 };
 
 // ---------------------------------------------------------------------------
-// Storage codecs: load a stored value as arithmetic type R, store R.
+// Storage codecs.  The store keeps, for every direction i and node n, the pair
+// (f_i, g_i) in one element P (double2 / float2 / half2 / bfloat162): both values
+// are pulled from the same source node, so one access moves both.  The deviation
+// stores hold (f_i - f_i^rest, g_i - g_i^rest) rounded to nearest even.
 // ---------------------------------------------------------------------------
 template <int ST> struct Codec;
 
 template <> struct Codec<ST_F64> {
-    using S = double;
+    using P = double2;
     using R = double;
-    __device__ __forceinline__ static R load(const S* p, size_t k, float) { return p[k]; }
-    __device__ __forceinline__ static R dec(S v, float) { return v; }
-    __device__ __forceinline__ static S enc(R v, float) { return v; }
+    __device__ __forceinline__ static void dec(P v, float, float, R& f, R& g) { f = v.x; g = v.y; }
+    __device__ __forceinline__ static P enc(R f, R g, float, float) { return make_double2(f, g); }
 };
 template <> struct Codec<ST_F32> {
-    using S = float;
+    using P = float2;
     using R = float;
-    __device__ __forceinline__ static R load(const S* p, size_t k, float) { return p[k]; }
-    __device__ __forceinline__ static R dec(S v, float) { return v; }
-    __device__ __forceinline__ static S enc(R v, float) { return v; }
+    __device__ __forceinline__ static void dec(P v, float, float, R& f, R& g) { f = v.x; g = v.y; }
+    __device__ __forceinline__ static P enc(R f, R g, float, float) { return make_float2(f, g); }
 };
 template <> struct Codec<ST_F16DEV> {
-    using S = __half;
+    using P = __half2;
     using R = float;
-    __device__ __forceinline__ static R dec(S v, float rest) { return rest + __half2float(v); }
-    __device__ __forceinline__ static R load(const S* p, size_t k, float rest) { return dec(p[k], rest); }
-    __device__ __forceinline__ static S enc(R v, float rest) { return __float2half_rn(v - rest); }
+    __device__ __forceinline__ static void dec(P v, float rf, float rg, R& f, R& g) {
+        const float2 d = __half22float2(v);
+        f = rf + d.x;
+        g = rg + d.y;
+    }
+    __device__ __forceinline__ static P enc(R f, R g, float rf, float rg) { return __floats2half2_rn(f - rf, g - rg); }
 };
 template <> struct Codec<ST_BF16DEV> {
-    using S = __nv_bfloat16;
+    using P = __nv_bfloat162;
     using R = float;
-    __device__ __forceinline__ static R dec(S v, float rest) { return rest + __bfloat162float(v); }
-    __device__ __forceinline__ static R load(const S* p, size_t k, float rest) { return dec(p[k], rest); }
-    __device__ __forceinline__ static S enc(R v, float rest) { return __float2bfloat16_rn(v - rest); }
+    __device__ __forceinline__ static void dec(P v, float rf, float rg, R& f, R& g) {
+        const float2 d = __bfloat1622float2(v);
+        f = rf + d.x;
+        g = rg + d.y;
+    }
+    __device__ __forceinline__ static P enc(R f, R g, float rf, float rg) {
+        return __floats2bfloat162_rn(f - rf, g - rg);
+    }
 };
 
 // ---------------------------------------------------------------------------

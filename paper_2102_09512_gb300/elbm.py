@@ -23,7 +23,7 @@ ELBM_D2Q9, ELBM_D3Q27 = 9, 27
 ELBM_BC_PERIODIC, ELBM_BC_ZEROGRAD = 0, 1
 ELBM_F64, ELBM_F32, ELBM_F16DEV, ELBM_BF16DEV = 0, 1, 2, 3
 ELBM_DERIV_UPWIND, ELBM_DERIV_CENTRAL = 0, 1
-ELBM_KERNEL_FUSED, ELBM_KERNEL_TWOPASS = 0, 1
+ELBM_KERNEL_FUSED, ELBM_KERNEL_TWOPASS, ELBM_KERNEL_FUSED_REREAD = 0, 1, 2
 
 STORES = {"f64": ELBM_F64, "f32": ELBM_F32, "f16dev": ELBM_F16DEV, "bf16dev": ELBM_BF16DEV}
 VALUE_BYTES = {ELBM_F64: 8, ELBM_F32: 4, ELBM_F16DEV: 2, ELBM_BF16DEV: 2}

@@ -116,7 +116,7 @@ def test_d2q9_parity(E, case, store, kernel):
     assert_parity(gpu_fields(E, c, steps, store, kernel), ref, TOL[store], (case, kernel, store))
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("case,store", PAIRS)
 def test_d3q27_parity(E, case, store, kernel):
     c = CASES_3D[case]()
@@ -125,12 +125,14 @@ def test_d3q27_parity(E, case, store, kernel):
     assert_parity(gpu_fields(E, c, steps, store, kernel), ref, TOL[store], (case, kernel, store))
 
 
-@pytest.mark.parametrize("tz", [1, 5, 7, 64])
-def test_d3q27_z_segments(E, tz):
-    """The z-segment length of the fused kernel changes nothing but the schedule."""
+@pytest.mark.parametrize("store", ["f64", "f32", "f16dev"])
+@pytest.mark.parametrize("tz", [1, 2, 5, 7, 64])
+def test_d3q27_z_segments(E, tz, store):
+    """The z-segment length of the fused kernels changes nothing but the schedule
+    (segments of 1 and 2 planes exercise the pipeline prologue and epilogue)."""
     c = CASES_3D["periodic"]()
     ref = oracle_fields(("3d", "periodic"), c, 40)
-    assert_parity(gpu_fields(E, c, 40, "f64", 0, tz=tz), ref, TOL["f64"], tz)
+    assert_parity(gpu_fields(E, c, 40, store, 0, tz=tz), ref, TOL[store], (tz, store))
 
 
 @pytest.mark.parametrize("D", [2, 3])
@@ -205,11 +207,12 @@ def test_checkpoint_restart_is_bitwise(E):
 
 def test_fused_and_twopass_agree(E):
     c = CASES_3D["periodic"]()
-    for store, tol in (("f64", 1e-14), ("f32", 1e-6)):
+    for store, tol in (("f64", 1e-14), ("f32", 1e-6), ("f16dev", 1e-6)):
         a = gpu_fields(E, c, 20, store, 0)
-        b = gpu_fields(E, c, 20, store, 1)
-        for x, y in zip(a, b):
-            assert rel_l2(x, y) <= tol, store
+        for kernel in (1, 2):
+            b = gpu_fields(E, c, 20, store, kernel)
+            for x, y in zip(a, b):
+                assert rel_l2(x, y) <= tol, (store, kernel)
 
 
 def test_nonphysical_state_is_reported_and_recoverable(E):
