@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libelbm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-diag-suppress", "177",
          "-I", CSRC, "-I", INCLUDE]
 STORES = [("f64", 0), ("f32", 1), ("f16", 2), ("bf16", 3)]
 
@@ -50,27 +50,28 @@ def _run(cmd):
     return r.stdout
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile (if sources changed) and return the path of libelbm.so."""
-    os.makedirs(BUILD, exist_ok=True)
-    stamp = os.path.join(BUILD, "digest.txt")
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir: str = BUILD) -> str:
+    """Compile (if sources changed) and return the path of libelbm.so (in out_dir)."""
+    os.makedirs(out_dir, exist_ok=True)
+    lib_path = os.path.join(out_dir, "libelbm.so")
+    stamp = os.path.join(out_dir, "digest.txt")
     digest = _sources_digest() + " ".join(extra_flags)
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp):
         with open(stamp) as fh:
             if fh.read() == digest:
-                return LIB
+                return lib_path
     exe = nvcc()
     jobs = []
     for D in (2, 3):
         for name, st in STORES:
-            obj = os.path.join(BUILD, f"elbm_d{D}_{name}.o")
+            obj = os.path.join(out_dir, f"elbm_d{D}_{name}.o")
             cmd = [exe, *ARCH, *FLAGS, *extra_flags, f"-DELBM_D={D}", f"-DELBM_ST={st}",
                    f"-DELBM_OPS_NAME=d{D}_{name}", "-c", os.path.join(CSRC, "elbm_kernels.cu"), "-o", obj]
             if verbose:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append((obj, cmd))
     for name in ("elbm_api", "elbm_noalloc"):
-        obj = os.path.join(BUILD, f"{name}.o")
+        obj = os.path.join(out_dir, f"{name}.o")
         jobs.append((obj, [exe, *ARCH, *FLAGS, *extra_flags, "-c", os.path.join(CSRC, f"{name}.cu"), "-o", obj]))
     workers = min(len(jobs), max(2, os.cpu_count() or 2))
     with cf.ThreadPoolExecutor(workers) as ex:
@@ -78,12 +79,12 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if verbose:
         for (obj, _), out in zip(jobs, outs):
             sys.stdout.write(f"--- {os.path.basename(obj)}\n{out}")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     _run([exe, *ARCH, "-shared", "-o", tmp, *[j[0] for j in jobs], "-lcudart"])
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_path)
     with open(stamp, "w") as fh:
         fh.write(digest)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":

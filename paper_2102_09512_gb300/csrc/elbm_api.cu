@@ -56,25 +56,6 @@ const Ops* pick_ops(int D, int store) {
     return nullptr;
 }
 
-bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
-
-// Rest state f^eq(rho0, 0, T0), g^eq(rho0, 0, T0) of the deviation stores.  With
-// u = 0 the per-axis factors are phi = (T/2, 1-T, T/2) and psi = (T^2/2, -T^2, T^2/2).
-void rest_state(int D, double rho0, double T0, double gamma, float* out) {
-    const int Q = D == 3 ? 27 : 9;
-    const double Cv = 1.0 / (gamma - 1.0);
-    const double phi[3] = {0.5 * T0, 1.0 - T0, 0.5 * T0};
-    const double psi[3] = {0.5 * T0 * T0, -T0 * T0, 0.5 * T0 * T0};
-    for (int i = 0; i < Q; ++i) {
-        const int a = i % 3, b = (i / 3) % 3, c = D == 3 ? i / 9 : 1;
-        const double pz = D == 3 ? phi[c] : 1.0, sz = D == 3 ? psi[c] : 0.0;
-        const double f = rho0 * phi[a] * phi[b] * pz;
-        const double g = rho0 * ((Cv * T0 * phi[a] + psi[a]) * phi[b] * pz + phi[a] * (psi[b] * pz + phi[b] * sz));
-        out[i] = (float)f;
-        out[Q + i] = (float)g;
-    }
-}
-
 __global__ void finalize_kernel(const double* __restrict__ partials, int nb, double* __restrict__ out) {
     double s[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0};
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
@@ -146,25 +127,12 @@ int elbm_create(const elbm_params* prm, elbm_handle** out) {
     if (!prm || !out) return ELBM_ERR_ARG;
     *out = nullptr;
     const elbm_params& p = *prm;
-    int D;
-    if (p.lattice == ELBM_D2Q9) D = 2;
-    else if (p.lattice == ELBM_D3Q27) D = 3;
-    else return ELBM_ERR_ARG;
-    if (p.nx < 1 || p.ny < 1 || p.nz < 1) return ELBM_ERR_ARG;
-    if (D == 2 && p.nz != 1) return ELBM_ERR_ARG;
-    const long long N = (long long)p.nx * p.ny * p.nz;
+    KParams kp;
+    int D = 0;
+    const int rc = fill_kparams(p, kp, &D);
+    if (rc != ELBM_OK) return rc;
+    const long long N = kp.N;
     if (N > (1LL << 31)) return ELBM_ERR_UNSUPPORTED;
-    if (!(std::isfinite(p.gamma) && p.gamma > 1.0)) return ELBM_ERR_ARG;
-    if (!finite_pos(p.Pr) || !finite_pos(p.mu0) || !finite_pos(p.T0) || !std::isfinite(p.mu_exp))
-        return ELBM_ERR_ARG;
-    for (int k = 0; k < 6; ++k)
-        if (p.bc[k] != ELBM_BC_PERIODIC && p.bc[k] != ELBM_BC_ZEROGRAD) return ELBM_ERR_ARG;
-    for (int a = 0; a < 3; ++a)
-        if ((p.bc[2 * a] == ELBM_BC_PERIODIC) != (p.bc[2 * a + 1] == ELBM_BC_PERIODIC)) return ELBM_ERR_ARG;
-    if (p.store < ELBM_F64 || p.store > ELBM_BF16DEV) return ELBM_ERR_ARG;
-    if (p.deriv != ELBM_DERIV_UPWIND && p.deriv != ELBM_DERIV_CENTRAL) return ELBM_ERR_ARG;
-    const bool dev = p.store == ELBM_F16DEV || p.store == ELBM_BF16DEV;
-    if (dev && (!finite_pos(p.rho_ref) || !finite_pos(p.T_ref) || p.T_ref >= 1.0)) return ELBM_ERR_ARG;
 
     elbm_handle* h = new (std::nothrow) elbm_handle();
     if (!h) return ELBM_ERR_ARG;
@@ -175,23 +143,8 @@ int elbm_create(const elbm_params* prm, elbm_handle** out) {
     h->ops = pick_ops(D, p.store);
     h->kernel = ELBM_KERNEL_FUSED;
 
-    KParams& k = h->kp;
-    std::memset(&k, 0, sizeof(k));
-    k.nx = p.nx;
-    k.ny = p.ny;
-    k.nz = p.nz;
-    k.per_x = p.bc[0] == ELBM_BC_PERIODIC;
-    k.per_y = p.bc[2] == ELBM_BC_PERIODIC;
-    k.per_z = p.bc[4] == ELBM_BC_PERIODIC;
-    k.N = N;
-    k.gm1 = p.gamma - 1.0;
-    k.Pr = p.Pr;
-    k.mu0 = p.mu0;
-    k.T0 = p.T0;
-    k.mu_exp = p.mu_exp;
-    k.deriv = p.deriv;
-    k.tz = p.nz < 32 ? p.nz : 32;
-    if (dev) rest_state(D, p.rho_ref, p.T_ref, p.gamma, k.rest32);
+    h->kp = kp;
+    const KParams& k = h->kp;
 
     h->pop_bytes = (size_t)2 * h->Q * (size_t)N * h->ops->value_bytes;
     AuxLayout& a = h->aux;

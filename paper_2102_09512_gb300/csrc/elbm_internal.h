@@ -4,9 +4,80 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <cstring>
+
+#include "elbm.h"
 #include "elbm_node.cuh"
 
 namespace elbm {
+
+// Validates a problem statement and fills the kernel parameters (host only, no CUDA
+// call, no allocation).  Returns ELBM_OK or ELBM_ERR_ARG; *D_out is 2 or 3.
+inline int fill_kparams(const elbm_params& p, KParams& k, int* D_out) {
+    auto finite_pos = [](double v) { return std::isfinite(v) && v > 0.0; };
+    int D;
+    if (p.lattice == ELBM_D2Q9) D = 2;
+    else if (p.lattice == ELBM_D3Q27) D = 3;
+    else return ELBM_ERR_ARG;
+    if (p.nx < 1 || p.ny < 1 || p.nz < 1 || (D == 2 && p.nz != 1)) return ELBM_ERR_ARG;
+    if (!(std::isfinite(p.gamma) && p.gamma > 1.0)) return ELBM_ERR_ARG;
+    if (!finite_pos(p.Pr) || !finite_pos(p.mu0) || !finite_pos(p.T0) || !std::isfinite(p.mu_exp))
+        return ELBM_ERR_ARG;
+    for (int f = 0; f < 6; ++f)
+        if (p.bc[f] != ELBM_BC_PERIODIC && p.bc[f] != ELBM_BC_ZEROGRAD) return ELBM_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if ((p.bc[2 * a] == ELBM_BC_PERIODIC) != (p.bc[2 * a + 1] == ELBM_BC_PERIODIC)) return ELBM_ERR_ARG;
+    if (p.store < ELBM_F64 || p.store > ELBM_BF16DEV) return ELBM_ERR_ARG;
+    if (p.deriv != ELBM_DERIV_UPWIND && p.deriv != ELBM_DERIV_CENTRAL) return ELBM_ERR_ARG;
+    const bool dev = p.store == ELBM_F16DEV || p.store == ELBM_BF16DEV;
+    if (dev && (!finite_pos(p.rho_ref) || !finite_pos(p.T_ref) || p.T_ref >= 1.0)) return ELBM_ERR_ARG;
+
+    std::memset(&k, 0, sizeof(k));
+    k.nx = p.nx;
+    k.ny = p.ny;
+    k.nz = p.nz;
+    k.per_x = p.bc[0] == ELBM_BC_PERIODIC;
+    k.per_y = p.bc[2] == ELBM_BC_PERIODIC;
+    k.per_z = p.bc[4] == ELBM_BC_PERIODIC;
+    k.N = (long long)p.nx * p.ny * p.nz;
+    k.gm1 = p.gamma - 1.0;
+    k.Pr = p.Pr;
+    k.mu0 = p.mu0;
+    k.T0 = p.T0;
+    k.mu_exp = p.mu_exp;
+    k.deriv = p.deriv;
+    k.tz = p.nz < 32 ? p.nz : 32;
+    if (dev) {
+        // Rest state f^eq(rho_ref, 0, T_ref), g^eq(rho_ref, 0, T_ref): with u = 0 the
+        // per-axis factors are phi = (T/2, 1-T, T/2) and psi = (T^2/2, -T^2, T^2/2).
+        const int Q = D == 3 ? 27 : 9;
+        const double T0 = p.T_ref, Cv = 1.0 / (p.gamma - 1.0);
+        const double phi[3] = {0.5 * T0, 1.0 - T0, 0.5 * T0};
+        const double psi[3] = {0.5 * T0 * T0, -T0 * T0, 0.5 * T0 * T0};
+        double srho = 0, sxx = 0, syy = 0, szz = 0, sE = 0;
+        for (int i = 0; i < Q; ++i) {
+            const int a = i % 3, b = (i / 3) % 3, c = D == 3 ? i / 9 : 1;
+            const double pz = D == 3 ? phi[c] : 1.0, sz = D == 3 ? psi[c] : 0.0;
+            k.rest32[i] = (float)(p.rho_ref * phi[a] * phi[b] * pz);
+            k.rest32[Q + i] = (float)(p.rho_ref * ((Cv * T0 * phi[a] + psi[a]) * phi[b] * pz +
+                                                   phi[a] * (psi[b] * pz + phi[b] * sz)));
+            // moment sums of the stored (rounded) rest values
+            srho += k.rest32[i];
+            if (a != 1) sxx += k.rest32[i];
+            if (b != 1) syy += k.rest32[i];
+            if (D == 3 && c != 1) szz += k.rest32[i];
+            sE += k.rest32[Q + i];
+        }
+        k.rest_rho = (float)srho;
+        k.rest_Pxx = (float)sxx;
+        k.rest_Pyy = (float)syy;
+        k.rest_Pzz = (float)szz;
+        k.rest_E = (float)sE;
+    }
+    *D_out = D;
+    return ELBM_OK;
+}
 
 // Layout of the auxiliary buffer (all offsets 256-byte aligned).
 struct AuxLayout {

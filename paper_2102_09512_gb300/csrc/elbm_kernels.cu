@@ -40,6 +40,7 @@ using Cd = Codec<kST>;
 using P = typename Cd::P;
 using R = typename Cd::R;
 constexpr int Q = Lat<kD>::Q;
+constexpr bool DEV = Cd::DEV;
 
 // ---------------------------------------------------------------------------
 // helpers
@@ -83,21 +84,21 @@ __device__ __forceinline__ size_t src_elem(const KParams& p, const PullRows& r, 
 __device__ __forceinline__ void gather(const KParams& p, const P* __restrict__ src, const PullRows& r,
                                        R* f, R* g) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) Cd::dec(src[src_elem(p, r, i)], p.rest32[i], p.rest32[Q + i], f[i], g[i]);
+    for (int i = 0; i < Q; ++i) Cd::dec(src[src_elem(p, r, i)], f[i], g[i]);
 }
 
 __device__ __forceinline__ void load_local(const KParams& p, const P* __restrict__ pop, long long n, R* f,
                                            R* g) {
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-        Cd::dec(pop[(size_t)i * (size_t)p.N + (size_t)n], p.rest32[i], p.rest32[Q + i], f[i], g[i]);
+        Cd::dec(pop[(size_t)i * (size_t)p.N + (size_t)n], f[i], g[i]);
 }
 
 __device__ __forceinline__ void store_node(const KParams& p, P* __restrict__ dst, long long n, const R* f,
                                            const R* g) {
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-        dst[(size_t)i * (size_t)p.N + (size_t)n] = Cd::enc(f[i], g[i], p.rest32[i], p.rest32[Q + i]);
+        dst[(size_t)i * (size_t)p.N + (size_t)n] = Cd::enc(f[i], g[i]);
 }
 
 // Totals of one node: rho, rho u_x, rho u_y, rho u_z, rho E.
@@ -107,13 +108,6 @@ __device__ __forceinline__ void node_totals(const Moments<R>& m, R rE, R v[5]) {
     v[2] = m.rho * m.uy;
     v[3] = m.rho * m.uz;
     v[4] = rE;
-}
-
-__device__ __forceinline__ R sum_g(const R* g) {
-    R s = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) s += g[i];
-    return s;
 }
 
 // Kahan-compensated running sum in the arithmetic type.
@@ -193,6 +187,13 @@ __global__ void init_kernel(const __grid_constant__ KParams p, const double* __r
               !isfinite(uy) || !isfinite(uz);
         R f[Q], g[Q];
         equilibria<kD, R>(r, ux, uy, uz, t, R(1) / R(p.gm1), f, g);
+        if constexpr (DEV) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                f[i] -= R(p.rest32[i]);
+                g[i] -= R(p.rest32[Q + i]);
+            }
+        }
         store_node(p, pop, n, f, g);
     }
     flag_if(bad, status);
@@ -207,7 +208,7 @@ __global__ void fields_kernel(const __grid_constant__ KParams p, const P* __rest
         R f[Q], g[Q];
         load_local(p, pop, n, f, g);
         Moments<R> m;
-        node_moments<kD, R, false>(f, g, R(p.gm1), m);
+        node_moments<kD, R, false, DEV>(f, g, p, m);
         rho[n] = m.rho;
         u[n] = m.ux;
         u[p.N + n] = m.uy;
@@ -235,6 +236,10 @@ __global__ void totals_kernel(const __grid_constant__ KParams p, const P* __rest
             if (cy_of(i) != 0) v[2] += cy_of(i) * fi;
             if (cz_of<kD>(i) != 0) v[3] += cz_of<kD>(i) * fi;
             v[4] += (double)g[i];
+        }
+        if constexpr (DEV) {   // moment sums of the rest state (no momentum)
+            v[0] += (double)p.rest_rho;
+            v[4] += (double)p.rest_E;
         }
 #pragma unroll
         for (int k = 0; k < 5; ++k) {   // Neumaier
@@ -265,7 +270,7 @@ __global__ void moments_kernel(const __grid_constant__ KParams p, const P* __res
     R f[Q], g[Q];
     gather(p, src, r, f, g);
     Moments<R> m;
-    node_moments<kD, R, false>(f, g, R(p.gm1), m);
+    node_moments<kD, R, false, DEV>(f, g, p, m);
     qf[n] = anomaly(m.rho, m.ux, m.T);
     qf[p.N + n] = anomaly(m.rho, m.uy, m.T);
     if (kD == 3) qf[2 * p.N + n] = anomaly(m.rho, m.uz, m.T);
@@ -288,7 +293,7 @@ __global__ void collide_kernel(const __grid_constant__ KParams p, const P* __res
         R f[Q], g[Q];
         gather(p, src, r, f, g);
         Moments<R> m;
-        node_moments<kD, R, true>(f, g, R(p.gm1), m);
+        node_moments<kD, R, true, DEV>(f, g, p, m);
         bad = nonphysical(m);
         const long long N = p.N;
         const int xm = map_axis(x - 1, p.nx, p.per_x), xp = map_axis(x + 1, p.nx, p.per_x);
@@ -303,10 +308,10 @@ __global__ void collide_kernel(const __grid_constant__ KParams p, const P* __res
                     qf[2 * N + node_index(p, x, y, zp)]);
         }
         R v[5];
-        node_totals(m, sum_g(g), v);
+        node_totals(m, m.rE, v);
 #pragma unroll
         for (int k = 0; k < 5; ++k) tot[k] = (double)v[k];
-        collide<kD, R>(f, g, m, Dx, Dy, Dz, p);
+        collide<kD, R, DEV>(f, g, m, Dx, Dy, Dz, p);
         store_node(p, dst, n, f, g);
     }
     flag_if(bad, status);
@@ -366,7 +371,7 @@ fused2d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
         PullRows r;
         pull_rows(p, x, y, 0, r);
         gather(p, src, r, f, g);
-        node_moments<kD, R, true>(f, g, R(p.gm1), m);
+        node_moments<kD, R, true, DEV>(f, g, p, m);
         qx[ty][tx + 1] = anomaly(m.rho, m.ux, m.T);
         qy[ty + 1][tx] = anomaly(m.rho, m.uy, m.T);
     }
@@ -379,7 +384,7 @@ fused2d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
             R hf[Q], hg[Q];
             gather(p, src, r, hf, hg);
             Moments<R> hm;
-            node_moments<kD, R, false>(hf, hg, R(p.gm1), hm);
+            node_moments<kD, R, false, DEV>(hf, hg, p, hm);
             if (axis == 1) qy[sy][sx] = anomaly(hm.rho, hm.uy, hm.T);
             else qx[sy][sx] = anomaly(hm.rho, hm.ux, hm.T);
         }
@@ -393,10 +398,10 @@ fused2d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
         const R Dx = dQ(p.deriv, m.ux, qx[ty][tx], qx[ty][tx + 1], qx[ty][tx + 2]);
         const R Dy = dQ(p.deriv, m.uy, qy[ty][tx], qy[ty + 1][tx], qy[ty + 2][tx]);
         R v[5];
-        node_totals(m, sum_g(g), v);
+        node_totals(m, m.rE, v);
 #pragma unroll
         for (int k = 0; k < 5; ++k) tot[k] = (double)v[k];
-        collide<kD, R>(f, g, m, Dx, Dy, R(0), p);
+        collide<kD, R, DEV>(f, g, m, Dx, Dy, R(0), p);
         store_node(p, dst, node_index(p, x, y, 0), f, g);
     }
     flag_if(bad, status);
@@ -410,7 +415,7 @@ __device__ __forceinline__ R direct_anomaly_z(const KParams& p, const P* __restr
     R f[Q], g[Q];
     gather(p, src, r, f, g);
     Moments<R> m;
-    node_moments<kD, R, false>(f, g, R(p.gm1), m);
+    node_moments<kD, R, false, DEV>(f, g, p, m);
     return anomaly(m.rho, m.uz, m.T);
 }
 
@@ -436,6 +441,11 @@ struct Pipe {
     static constexpr size_t buf_bytes = (size_t)NB * Q * NS * sizeof(P);
     static constexpr size_t q_bytes = (size_t)2 * (TY * (TX + 2) + (TY + 2) * TX) * sizeof(R);
     static constexpr size_t smem_bytes = buf_bytes + q_bytes;
+};
+
+template <int TY, int NB>
+struct PipeBytes {
+    static constexpr size_t value = Pipe<TY, NB>::smem_bytes;
 };
 
 template <int TY, int NB, int MINB>
@@ -479,14 +489,13 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
         }
         cp_async_commit();
     };
-    // moments of the node in slot `slot` of buffer sb; returns rho E
-    auto slot_moments = [&](int sb, int slot, Moments<R>& m) -> R {
+    // moments of the node in slot `slot` of buffer sb
+    auto slot_moments = [&](int sb, int slot, Moments<R>& m) {
         const P* bb = buf + (size_t)sb * Q * NS + slot;
         R f[Q], g[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], p.rest32[i], p.rest32[Q + i], f[i], g[i]);
-        node_moments<kD, R, true>(f, g, R(p.gm1), m);
-        return sum_g(g);
+        for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], f[i], g[i]);
+        node_moments<kD, R, true, DEV>(f, g, p, m);
     };
 
     Acc5 acc;
@@ -499,11 +508,10 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
     issue_plane(zb, 0, true);
     issue_plane(map_axis(zb + 1, p.nz, p.per_z), 1 % NB, zb + 1 < ze);
     Moments<R> m_cur, m_next;
-    R rE_cur = R(0), rE_next = R(0);
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     __syncthreads();
     if (active) {
-        rE_cur = slot_moments(0, tid, m_cur);
+        slot_moments(0, tid, m_cur);
         QX(0, ty, tx + 1) = anomaly(m_cur.rho, m_cur.ux, m_cur.T);
         QY(0, ty + 1, tx) = anomaly(m_cur.rho, m_cur.uy, m_cur.T);
         qz_cur = anomaly(m_cur.rho, m_cur.uz, m_cur.T);
@@ -526,7 +534,7 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
         if (NB == 3 && z + 2 <= ze) issue_plane(map_axis(z + 2, p.nz, p.per_z), (k + 2) % NB, z + 2 < ze);
 
         if (active) {
-            rE_next = slot_moments(sn, tid, m_next);
+            slot_moments(sn, tid, m_next);
             qz_next = anomaly(m_next.rho, m_next.uz, m_next.T);
             if (!last) {
                 QX(bq ^ 1, ty, tx + 1) = anomaly(m_next.rho, m_next.ux, m_next.T);
@@ -545,7 +553,7 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
         if (active) {
             const P* bb = buf + (size_t)sz * Q * NS + tid;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], p.rest32[i], p.rest32[Q + i], f[i], g[i]);
+            for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], f[i], g[i]);
         }
         if (NB == 2) {
             __syncthreads();                                                 // [C]
@@ -557,13 +565,12 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
             const R Dy = dQ(p.deriv, m_cur.uy, QY(bq, ty, tx), QY(bq, ty + 1, tx), QY(bq, ty + 2, tx));
             const R Dz = dQ(p.deriv, m_cur.uz, qz_prev, qz_cur, qz_next);
             R v[5];
-            node_totals(m_cur, rE_cur, v);
+            node_totals(m_cur, m_cur.rE, v);
             acc.add(v);
-            collide<kD, R>(f, g, m_cur, Dx, Dy, Dz, p);
+            collide<kD, R, DEV>(f, g, m_cur, Dx, Dy, Dz, p);
             store_node(p, dst, node_index(p, x, y, z), f, g);
         }
         m_cur = m_next;
-        rE_cur = rE_next;
         qz_prev = qz_cur;
         qz_cur = qz_next;
     }
@@ -601,7 +608,7 @@ fused3d_reread_kernel(const __grid_constant__ KParams p, const P* __restrict__ s
             R f[Q], g[Q];
             gather(p, src, r, f, g);
             Moments<R> m;
-            node_moments<kD, R, false>(f, g, R(p.gm1), m);
+            node_moments<kD, R, false, DEV>(f, g, p, m);
             if (with_xy) {
                 qx[b][ty][tx + 1] = anomaly(m.rho, m.ux, m.T);
                 qy[b][ty + 1][tx] = anomaly(m.rho, m.uy, m.T);
@@ -614,7 +621,7 @@ fused3d_reread_kernel(const __grid_constant__ KParams p, const P* __restrict__ s
             R f[Q], g[Q];
             gather(p, src, r, f, g);
             Moments<R> m;
-            node_moments<kD, R, false>(f, g, R(p.gm1), m);
+            node_moments<kD, R, false, DEV>(f, g, p, m);
             if (haxis == 1) qy[b][hsy][hsx] = anomaly(m.rho, m.uy, m.T);
             else qx[b][hsy][hsx] = anomaly(m.rho, m.ux, m.T);
         }
@@ -638,15 +645,15 @@ fused3d_reread_kernel(const __grid_constant__ KParams p, const P* __restrict__ s
             R f[Q], g[Q];
             gather(p, src, r, f, g);
             Moments<R> m;
-            node_moments<kD, R, true>(f, g, R(p.gm1), m);
+            node_moments<kD, R, true, DEV>(f, g, p, m);
             bad |= nonphysical(m);
             const R Dx = dQ(p.deriv, m.ux, qx[b][ty][tx], qx[b][ty][tx + 1], qx[b][ty][tx + 2]);
             const R Dy = dQ(p.deriv, m.uy, qy[b][ty][tx], qy[b][ty + 1][tx], qy[b][ty + 2][tx]);
             const R Dz = dQ(p.deriv, m.uz, qz_prev, qz_cur, qz_next);
             R v[5];
-            node_totals(m, sum_g(g), v);
+            node_totals(m, m.rE, v);
             acc.add(v);
-            collide<kD, R>(f, g, m, Dx, Dy, Dz, p);
+            collide<kD, R, DEV>(f, g, m, Dx, Dy, Dz, p);
             store_node(p, dst, node_index(p, x, y, z), f, g);
         }
         qz_prev = qz_cur;
@@ -664,14 +671,24 @@ fused3d_reread_kernel(const __grid_constant__ KParams p, const P* __restrict__ s
 // ---------------------------------------------------------------------------
 constexpr int kThreads = 256;
 constexpr int kTY2 = 8;                  // D2Q9 fused tile 32 x 8
-constexpr int kTY3 = 8;                  // D3Q27 fused tiles 32 x 8
+#ifndef ELBM_TY3
+#define ELBM_TY3 8
+#endif
+constexpr int kTY3 = ELBM_TY3;           // D3Q27 fused tiles 32 x kTY3
 constexpr int kTotalsBlocks = 2 * 152;   // totals_kernel grid (grid-stride)
-// Pipelined D3Q27 kernel per store: FP32 keeps three plane buffers (218 KB, one CTA
-// per SM, up to 255 registers); FP16/BF16 pairs are half the size, so two buffers
-// and two CTAs per SM; FP64 uses the re-read kernel (its plane buffers would not fit).
+// Pipelined D3Q27 kernel per store: two plane buffers.  FP32 pairs make them 145 KB
+// (one CTA per SM, up to 255 registers; a third buffer would leave L1 almost no
+// room and measured 35 % slower); FP16/BF16 pairs are half the size (two CTAs per
+// SM); FP64 uses the re-read kernel (its plane buffers would not fit).
+#ifndef ELBM_PIPE_NB_F32
+#define ELBM_PIPE_NB_F32 2
+#endif
+#ifndef ELBM_PIPE_NB_F16
+#define ELBM_PIPE_NB_F16 2
+#endif
 constexpr bool kPipe = (kST != ST_F64);
-constexpr int kNB = (kST == ST_F32) ? 3 : 2;
-constexpr int kMinB = (kST == ST_F32) ? 1 : 2;
+constexpr int kNB = (kST == ST_F32) ? ELBM_PIPE_NB_F32 : ELBM_PIPE_NB_F16;
+constexpr int kMinB = (PipeBytes<kTY3, kNB>::value * 2 + 2048 <= 228 * 1024) ? 2 : 1;
 using PipeCfg = Pipe<kTY3, kNB>;
 
 inline unsigned blocks_1d(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
@@ -724,10 +741,12 @@ cudaError_t launch_twopass(const KParams& p, const void* src, void* dst, void* q
     return cudaGetLastError();
 }
 
+// A template so that the branch of the other lattice is never instantiated.
+template <int DD>
 cudaError_t launch_fused(const KParams& p, const void* src, void* dst, double* partials, int* nblocks,
                          int* status, cudaStream_t s, long long* launches, bool reread) {
     const dim3 grid = fused_grid(p);
-    if constexpr (kD == 2) {
+    if constexpr (DD == 2) {
         fused2d_kernel<kTY2><<<grid, dim3(TX, kTY2), 0, s>>>(p, (const P*)src, (P*)dst, partials, status);
     } else {
         bool launched = false;
@@ -755,12 +774,12 @@ cudaError_t launch_fused(const KParams& p, const void* src, void* dst, double* p
 
 cudaError_t launch_fused_default(const KParams& p, const void* src, void* dst, double* partials, int* nblocks,
                                  int* status, cudaStream_t s, long long* launches) {
-    return launch_fused(p, src, dst, partials, nblocks, status, s, launches, false);
+    return launch_fused<kD>(p, src, dst, partials, nblocks, status, s, launches, false);
 }
 
 cudaError_t launch_fused_reread(const KParams& p, const void* src, void* dst, double* partials, int* nblocks,
                                 int* status, cudaStream_t s, long long* launches) {
-    return launch_fused(p, src, dst, partials, nblocks, status, s, launches, true);
+    return launch_fused<kD>(p, src, dst, partials, nblocks, status, s, launches, true);
 }
 
 cudaError_t launch_totals(const KParams& p, const void* pop, double* partials, int* nblocks, cudaStream_t s,

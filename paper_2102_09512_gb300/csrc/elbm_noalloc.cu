@@ -49,8 +49,6 @@ const Ops* ops_for(int D, int store) {
     return nullptr;
 }
 
-bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
-
 // Device address of the scratch array on the current device (set-up on first use).
 int scratch_address(void** out) {
     int dev = -1;
@@ -71,54 +69,12 @@ extern "C" int elbm_step_noalloc(const elbm_params* prm, const void* src, void* 
     if (!prm || !src || !dst || src == dst) return ELBM_ERR_ARG;
     if (((uintptr_t)src | (uintptr_t)dst) % kAlign) return ELBM_ERR_ARG;
     const elbm_params& p = *prm;
-    int D;
-    if (p.lattice == ELBM_D2Q9) D = 2;
-    else if (p.lattice == ELBM_D3Q27) D = 3;
-    else return ELBM_ERR_ARG;
-    if (p.nx < 1 || p.ny < 1 || p.nz < 1 || (D == 2 && p.nz != 1)) return ELBM_ERR_ARG;
-    if (!(std::isfinite(p.gamma) && p.gamma > 1.0)) return ELBM_ERR_ARG;
-    if (!finite_pos(p.Pr) || !finite_pos(p.mu0) || !finite_pos(p.T0) || !std::isfinite(p.mu_exp))
-        return ELBM_ERR_ARG;
-    for (int k = 0; k < 6; ++k)
-        if (p.bc[k] != ELBM_BC_PERIODIC && p.bc[k] != ELBM_BC_ZEROGRAD) return ELBM_ERR_ARG;
-    for (int a = 0; a < 3; ++a)
-        if ((p.bc[2 * a] == ELBM_BC_PERIODIC) != (p.bc[2 * a + 1] == ELBM_BC_PERIODIC)) return ELBM_ERR_ARG;
-    if (p.store < ELBM_F64 || p.store > ELBM_BF16DEV) return ELBM_ERR_ARG;
-    if (p.deriv != ELBM_DERIV_UPWIND && p.deriv != ELBM_DERIV_CENTRAL) return ELBM_ERR_ARG;
-    const bool dev = p.store == ELBM_F16DEV || p.store == ELBM_BF16DEV;
-    if (dev && (!finite_pos(p.rho_ref) || !finite_pos(p.T_ref) || p.T_ref >= 1.0)) return ELBM_ERR_ARG;
+    KParams k;
+    int D = 0;
+    const int vrc = fill_kparams(p, k, &D);
+    if (vrc != ELBM_OK) return vrc;
     const Ops* ops = ops_for(D, p.store);
     if (!ops) return ELBM_ERR_ARG;
-
-    KParams k;
-    std::memset(&k, 0, sizeof(k));
-    k.nx = p.nx;
-    k.ny = p.ny;
-    k.nz = p.nz;
-    k.per_x = p.bc[0] == ELBM_BC_PERIODIC;
-    k.per_y = p.bc[2] == ELBM_BC_PERIODIC;
-    k.per_z = p.bc[4] == ELBM_BC_PERIODIC;
-    k.N = (long long)p.nx * p.ny * p.nz;
-    k.gm1 = p.gamma - 1.0;
-    k.Pr = p.Pr;
-    k.mu0 = p.mu0;
-    k.T0 = p.T0;
-    k.mu_exp = p.mu_exp;
-    k.deriv = p.deriv;
-    k.tz = p.nz < 32 ? p.nz : 32;
-    if (dev) {   // rest state f^eq(rho_ref, 0, T_ref), g^eq(rho_ref, 0, T_ref) of the deviation stores
-        const int Q = D == 3 ? 27 : 9;
-        const double T0 = p.T_ref, Cv = 1.0 / (p.gamma - 1.0);
-        const double phi[3] = {0.5 * T0, 1.0 - T0, 0.5 * T0};
-        const double psi[3] = {0.5 * T0 * T0, -T0 * T0, 0.5 * T0 * T0};
-        for (int i = 0; i < Q; ++i) {
-            const int a = i % 3, b = (i / 3) % 3, c = D == 3 ? i / 9 : 1;
-            const double pz = D == 3 ? phi[c] : 1.0, sz = D == 3 ? psi[c] : 0.0;
-            k.rest32[i] = (float)(p.rho_ref * phi[a] * phi[b] * pz);
-            k.rest32[Q + i] = (float)(p.rho_ref * ((Cv * T0 * phi[a] + psi[a]) * phi[b] * pz +
-                                                   phi[a] * (psi[b] * pz + phi[b] * sz)));
-        }
-    }
 
     // scratch layout: status word | per-CTA partials | Q~ field
     const size_t status_off = 0;

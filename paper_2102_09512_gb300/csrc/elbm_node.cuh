@@ -30,51 +30,56 @@ struct KParams {
     double gm1;                  // gamma - 1  (so Cv = 1 / gm1)
     double Pr, mu0, T0, mu_exp;
     int deriv;                   // 0 upwind, 1 central
-    int tz;                      // z-segment length of the fused 3D kernel
-    float rest32[54];            // rest-state populations (f then g) for deviation stores
+    int tz;                      // z-segment length of the fused 3D kernels
+    float rest32[54];            // rest-state populations (f then g) of the deviation stores
+    float rest_rho, rest_Pxx, rest_Pyy, rest_Pzz, rest_E;   // their moment sums
 };
 
 // ---------------------------------------------------------------------------
 // Storage codecs.  The store keeps, for every direction i and node n, the pair
 // (f_i, g_i) in one element P (double2 / float2 / half2 / bfloat162): both values
 // are pulled from the same source node, so one access moves both.  The deviation
-// stores hold (f_i - f_i^rest, g_i - g_i^rest) rounded to nearest even.
+// stores (DEV) hold (f_i - f_i^rest, g_i - g_i^rest) rounded to nearest even; the
+// kernels keep working on these raw stored values (see node_moments and collide),
+// so decoding is a conversion only.
 // ---------------------------------------------------------------------------
 template <int ST> struct Codec;
 
 template <> struct Codec<ST_F64> {
     using P = double2;
     using R = double;
-    __device__ __forceinline__ static void dec(P v, float, float, R& f, R& g) { f = v.x; g = v.y; }
-    __device__ __forceinline__ static P enc(R f, R g, float, float) { return make_double2(f, g); }
+    static constexpr bool DEV = false;
+    __device__ __forceinline__ static void dec(P v, R& f, R& g) { f = v.x; g = v.y; }
+    __device__ __forceinline__ static P enc(R f, R g) { return make_double2(f, g); }
 };
 template <> struct Codec<ST_F32> {
     using P = float2;
     using R = float;
-    __device__ __forceinline__ static void dec(P v, float, float, R& f, R& g) { f = v.x; g = v.y; }
-    __device__ __forceinline__ static P enc(R f, R g, float, float) { return make_float2(f, g); }
+    static constexpr bool DEV = false;
+    __device__ __forceinline__ static void dec(P v, R& f, R& g) { f = v.x; g = v.y; }
+    __device__ __forceinline__ static P enc(R f, R g) { return make_float2(f, g); }
 };
 template <> struct Codec<ST_F16DEV> {
     using P = __half2;
     using R = float;
-    __device__ __forceinline__ static void dec(P v, float rf, float rg, R& f, R& g) {
+    static constexpr bool DEV = true;
+    __device__ __forceinline__ static void dec(P v, R& f, R& g) {
         const float2 d = __half22float2(v);
-        f = rf + d.x;
-        g = rg + d.y;
+        f = d.x;
+        g = d.y;
     }
-    __device__ __forceinline__ static P enc(R f, R g, float rf, float rg) { return __floats2half2_rn(f - rf, g - rg); }
+    __device__ __forceinline__ static P enc(R f, R g) { return __floats2half2_rn(f, g); }
 };
 template <> struct Codec<ST_BF16DEV> {
     using P = __nv_bfloat162;
     using R = float;
-    __device__ __forceinline__ static void dec(P v, float rf, float rg, R& f, R& g) {
+    static constexpr bool DEV = true;
+    __device__ __forceinline__ static void dec(P v, R& f, R& g) {
         const float2 d = __bfloat1622float2(v);
-        f = rf + d.x;
-        g = rg + d.y;
+        f = d.x;
+        g = d.y;
     }
-    __device__ __forceinline__ static P enc(R f, R g, float rf, float rg) {
-        return __floats2bfloat162_rn(f - rf, g - rg);
-    }
+    __device__ __forceinline__ static P enc(R f, R g) { return __floats2bfloat162_rn(f, g); }
 };
 
 // ---------------------------------------------------------------------------
@@ -96,17 +101,27 @@ __device__ __forceinline__ int map_axis(int x, int n, int periodic) {
     return x;
 }
 
+// Division in the arithmetic type: exact for FP64, the fast hardware form for FP32
+// (a few ulp; every quotient here is of moderate magnitude).
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double qpow(double a, double b) { return pow(a, b); }
+__device__ __forceinline__ float qpow(float a, float b) { return __powf(a, b); }
+
 // ---------------------------------------------------------------------------
 // Moments
 // ---------------------------------------------------------------------------
 template <typename R> struct Moments {
-    R rho, ux, uy, uz, T;
+    R rho, ux, uy, uz, T, rE;
     R Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;   // sum c c f (pre-collision)
 };
 
 // rho, rho u and the pressure tensor from f; rho E from g; T from E = Cv T + u^2/2.
-template <int D, typename R, bool FULL>
-__device__ __forceinline__ void node_moments(const R* f, const R* g, R gm1, Moments<R>& m) {
+// f, g are the raw stored values; for the deviation stores (DEV) the moment sums of
+// the rest state are added (the rest state carries no momentum and no off-diagonal
+// stress, by symmetry).
+template <int D, typename R, bool FULL, bool DEV>
+__device__ __forceinline__ void node_moments(const R* f, const R* g, const KParams& p, Moments<R>& m) {
     constexpr int NC = Lat<D>::NC;
     // per (b, c) row sums over c_x
     R t[3][3], d[3][3], e[3][3];
@@ -142,13 +157,21 @@ __device__ __forceinline__ void node_moments(const R* f, const R* g, R gm1, Mome
     R rE = 0;
 #pragma unroll
     for (int i = 0; i < Lat<D>::Q; ++i) rE += g[i];
-    const R inv = R(1) / rho;
+    if constexpr (DEV) {
+        rho += R(p.rest_rho);
+        rE += R(p.rest_E);
+        Pxx += R(p.rest_Pxx);
+        Pyy += R(p.rest_Pyy);
+        Pzz += R(p.rest_Pzz);
+    }
+    const R inv = qdiv(R(1), rho);
     m.rho = rho;
+    m.rE = rE;
     m.ux = jx * inv;
     m.uy = jy * inv;
     m.uz = jz * inv;
     const R u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
-    m.T = (rE * inv - R(0.5) * u2) * gm1;
+    m.T = (rE * inv - R(0.5) * u2) * R(p.gm1);
     if (FULL) {
         m.Pxx = Pxx; m.Pyy = Pyy; m.Pzz = Pzz;
         m.Pxy = Pxy; m.Pxz = Pxz; m.Pyz = Pyz;
@@ -206,17 +229,15 @@ __device__ __forceinline__ void gfactors(R u, R T, R phi[3], R ps[3]) {
     ps[2] = R(0.5) * (s + o);
 }
 
-// Equilibria f^eq and g^eq of (rho, u, T) into f, g (used for initialisation and
-// for the rest state of the deviation stores).
+// Equilibria f^eq and g^eq of (rho, u, T) into f, g (full populations; used for
+// initialisation).
 template <int D, typename R>
 __device__ __forceinline__ void equilibria(R rho, R ux, R uy, R uz, R T, R Cv, R* f, R* g) {
-    R X[3], Y[3], Z[3], px[3], py[3], pz[3], sx[3], sy[3], sz[3];
+    R X[3], Y[3], Z[3], sx[3], sy[3], sz[3];
     gfactors(ux, T, X, sx);
     gfactors(uy, T, Y, sy);
     if (D == 3) gfactors(uz, T, Z, sz);
     else { Z[0] = Z[2] = 0; Z[1] = 1; sz[0] = sz[1] = sz[2] = 0; }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) { px[a] = X[a]; }
     const R CvT = Cv * T;
 #pragma unroll
     for (int c = 0; c < Lat<D>::NC; ++c) {
@@ -228,44 +249,53 @@ __device__ __forceinline__ void equilibria(R rho, R ux, R uy, R uz, R T, R Cv, R
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const int i = a + 3 * b + 9 * c;
-                f[i] = rho * px[a] * A;
+                f[i] = rho * X[a] * A;
                 g[i] = rho * ((CvT * X[a] + sx[a]) * A + X[a] * B);
             }
         }
     }
 }
 
-// One collision in place.  D_a is the discrete derivative of Q~_aaa at the node.
-template <int D, typename R>
+// One collision in place on the raw stored values f, g (populations, or their
+// deviations from the rest state when DEV).  D_a is the discrete derivative of
+// Q~_aaa at the node.  The BGK updates are written as
+//   f_i <- (1 - w) f_i + w f^ex_i,   g_i <- (1 - w1) g_i + w1 g^eq_i + corrections,
+// with w and w1 folded into the row factors of the product forms; for DEV the rest
+// state r_i is carried as (1 - w)(r_i + d_i) + w f^ex_i - r_i = (1 - w) d_i +
+// w (f^ex_i - r_i).
+template <int D, typename R, bool DEV>
 __device__ __forceinline__ void collide(R* f, R* g, const Moments<R>& m, R Dx, R Dy, R Dz,
                                         const KParams& p) {
     const R rho = m.rho, T = m.T, ux = m.ux, uy = m.uy, uz = m.uz;
     // relaxation rates (Eqs. mu, Pr) from the local pressure P = rho T
     R mu = R(p.mu0);
-    if (p.mu_exp != 0.0) mu = mu * pow(T / R(p.T0), R(p.mu_exp));
+    if (p.mu_exp != 0.0) mu = mu * qpow(T * R(1.0 / p.T0), R(p.mu_exp));
     const R P = rho * T;
-    const R w = R(2) * P / (R(2) * mu + P);
+    const R w = qdiv(R(2) * P, R(2) * mu + P);
     const R Pr = R(p.Pr);
-    const R w1 = R(2) * Pr * w / (R(2) - w + Pr * w);
-    const R Cv = R(1) / R(p.gm1);
+    const R w1 = qdiv(R(2) * Pr * w, R(2) - w + Pr * w);
+    const R Cv = R(1.0 / p.gm1);
 
     // extended f-equilibrium (Eqs. Pa_star, extf)
-    const R k = (R(2) - w) / (R(2) * rho * w);
+    const R k = qdiv(R(2) - w, R(2) * rho * w);
     R X[3], Y[3], Z[3];
     psi3(ux, T + ux * ux + k * Dx, X);
     psi3(uy, T + uy * uy + k * Dy, Y);
     if (D == 3) psi3(uz, T + uz * uz + k * Dz, Z);
     else { Z[0] = Z[2] = 0; Z[1] = 1; }
+    const R omw = R(1) - w, wr = w * rho;
 #pragma unroll
     for (int c = 0; c < Lat<D>::NC; ++c) {
         const int cc = (D == 3) ? c : 1;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            const R yz = rho * Y[b] * Z[cc];
+            const R yz = wr * Y[b] * Z[cc];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const int i = a + 3 * b + 9 * c;
-                f[i] = f[i] + w * (X[a] * yz - f[i]);
+                R t = X[a] * yz;
+                if constexpr (DEV) t = fma(-w, R(p.rest32[i]), t);
+                f[i] = fma(omw, f[i], t);
             }
         }
     }
@@ -280,18 +310,21 @@ __device__ __forceinline__ void collide(R* f, R* g, const Moments<R>& m, R Dx, R
     R ax[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) ax[a] = CvT * gx[a] + sx[a];
+    const R omw1 = R(1) - w1, w1r = w1 * rho;
+    constexpr int Q = Lat<D>::Q;
 #pragma unroll
     for (int c = 0; c < Lat<D>::NC; ++c) {
         const int cc = (D == 3) ? c : 1;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            const R A = rho * gy[b] * gz[cc];
-            const R B = rho * (sy[b] * gz[cc] + gy[b] * sz[cc]);
+            const R A = w1r * gy[b] * gz[cc];
+            const R B = w1r * (sy[b] * gz[cc] + gy[b] * sz[cc]);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const int i = a + 3 * b + 9 * c;
-                const R geq = ax[a] * A + gx[a] * B;
-                g[i] = g[i] + w1 * (geq - g[i]);
+                R t = fma(ax[a], A, gx[a] * B);
+                if constexpr (DEV) t = fma(-w1, R(p.rest32[Q + i]), t);
+                g[i] = fma(omw1, g[i], t);
             }
         }
     }

@@ -206,8 +206,11 @@ def test_checkpoint_restart_is_bitwise(E):
 
 
 def test_fused_and_twopass_agree(E):
+    """The three schedules compute the same arithmetic per node in different kernels;
+    compiler contraction choices differ at the last bit, which FP64 and FP32 keep at
+    rounding level and FP16 storage can turn into one-ulp differences per step."""
     c = CASES_3D["periodic"]()
-    for store, tol in (("f64", 1e-14), ("f32", 1e-6), ("f16dev", 1e-6)):
+    for store, tol in (("f64", 1e-14), ("f32", 1e-6), ("f16dev", TOL["f16dev"])):
         a = gpu_fields(E, c, 20, store, 0)
         for kernel in (1, 2):
             b = gpu_fields(E, c, 20, store, kernel)
