@@ -110,7 +110,10 @@ __device__ __forceinline__ void node_totals(const Moments<R>& m, R rE, R v[5]) {
     v[4] = rE;
 }
 
-// Kahan-compensated running sum in the arithmetic type.
+// Per-thread running sum of the node totals over the planes of a z segment:
+// Kahan-compensated in FP64; in FP32 a plain sum (at most p.tz terms of per-node
+// values that are themselves FP32 results), which saves the registers of the
+// compensation terms.
 struct Acc5 {
     R s[5], c[5];
     __device__ __forceinline__ void zero() {
@@ -120,10 +123,14 @@ struct Acc5 {
     __device__ __forceinline__ void add(const R v[5]) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            const R y = v[k] - c[k];
-            const R t = s[k] + y;
-            c[k] = (t - s[k]) - y;
-            s[k] = t;
+            if constexpr (sizeof(R) == 8) {
+                const R y = v[k] - c[k];
+                const R t = s[k] + y;
+                c[k] = (t - s[k]) - y;
+                s[k] = t;
+            } else {
+                s[k] += v[k];
+            }
         }
     }
 };

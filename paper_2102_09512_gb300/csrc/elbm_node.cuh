@@ -135,28 +135,40 @@ __device__ __forceinline__ void node_moments(const R* f, const R* g, const KPara
             d[b][c] = hi - lo;
             t[b][c] = e[b][c] + mid;
         }
-    R rho = 0, jx = 0, Pxx = 0;
+    // sums over c_z first (columns b), then over c_y: depth 2 + 2
+    R tb[3], db[3], eb[3];
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) { rho += t[b][c]; jx += d[b][c]; Pxx += e[b][c]; }
-    R tyh = 0, tyl = 0, dyh = 0, dyl = 0;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) { tyh += t[2][c]; tyl += t[0][c]; dyh += d[2][c]; dyl += d[0][c]; }
-    R jy = tyh - tyl, Pyy = tyh + tyl, Pxy = dyh - dyl;
+    for (int b = 0; b < 3; ++b) {
+        tb[b] = t[b][0];
+        db[b] = d[b][0];
+        eb[b] = e[b][0];
+        if (D == 3) {
+            tb[b] = (t[b][0] + t[b][2]) + t[b][1];
+            db[b] = (d[b][0] + d[b][2]) + d[b][1];
+            eb[b] = (e[b][0] + e[b][2]) + e[b][1];
+        }
+    }
+    const R rho_ = (tb[0] + tb[2]) + tb[1];
+    R rho = rho_, jx = (db[0] + db[2]) + db[1], Pxx = (eb[0] + eb[2]) + eb[1];
+    R jy = tb[2] - tb[0], Pyy = tb[2] + tb[0], Pxy = db[2] - db[0];
     R jz = 0, Pzz = 0, Pxz = 0, Pyz = 0;
     if (D == 3) {
-        R tzh = 0, tzl = 0, dzh = 0, dzl = 0;
-#pragma unroll
-        for (int b = 0; b < 3; ++b) { tzh += t[b][2]; tzl += t[b][0]; dzh += d[b][2]; dzl += d[b][0]; }
+        const R tzh = (t[0][2] + t[2][2]) + t[1][2], tzl = (t[0][0] + t[2][0]) + t[1][0];
+        const R dzh = (d[0][2] + d[2][2]) + d[1][2], dzl = (d[0][0] + d[2][0]) + d[1][0];
         jz = tzh - tzl;
         Pzz = tzh + tzl;
         Pxz = dzh - dzl;
         Pyz = (t[2][2] - t[0][2]) - (t[2][0] - t[0][0]);
     }
-    R rE = 0;
+    // sum of g as a balanced tree (short dependency chains)
+    R gs[Lat<D>::Q];
 #pragma unroll
-    for (int i = 0; i < Lat<D>::Q; ++i) rE += g[i];
+    for (int i = 0; i < Lat<D>::Q; ++i) gs[i] = g[i];
+#pragma unroll
+    for (int w = 1; w < Lat<D>::Q; w *= 2)
+#pragma unroll
+        for (int i = 0; i + w < Lat<D>::Q; i += 2 * w) gs[i] += gs[i + w];
+    R rE = gs[0];
     if constexpr (DEV) {
         rho += R(p.rest_rho);
         rE += R(p.rest_E);
