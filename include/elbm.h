@@ -183,6 +183,49 @@ int elbm_step_noalloc(const elbm_params *params, const void *src, void *dst, voi
 /* Frees the handle (not the caller's buffers). */
 int elbm_destroy(elbm_handle *h);
 
+/* ---------------------------------------------------------------------------
+ * Ensembles: n independent D2Q9 lattices of uneven sizes (the paper's 2D cases run
+ * side by side, e.g. a sweep of Mach numbers and grid sizes), all with the same
+ * store kind, kept back to back in one pair of population stores.  Each instance
+ * follows exactly the single-lattice update above.
+ * ------------------------------------------------------------------------- */
+typedef struct elbm_ensemble elbm_ensemble;
+
+typedef enum {
+    ELBM_ENSEMBLE_PERSISTENT = 0,   /* one launch per step over the tiles of all instances */
+    ELBM_ENSEMBLE_PER_INSTANCE = 1  /* one fused launch per instance per step               */
+} elbm_ensemble_mode;
+
+/* Validates params[0..n-1] (each as for elbm_create; D2Q9 only, one store kind,
+ * 1 <= n <= 1024) and creates the ensemble.  Host-only. */
+int elbm_ensemble_create(const elbm_params *params, int n, elbm_ensemble **out);
+int elbm_ensemble_bytes_required(const elbm_ensemble *e, size_t *pop_bytes, size_t *aux_bytes);
+/* Binds caller-owned device buffers (256-byte aligned) and a stream; copies the
+ * instance tables into the auxiliary buffer (synchronising). */
+int elbm_ensemble_bind(elbm_ensemble *e, void *pop_a, void *pop_b, void *aux, void *stream);
+/* Initial state of instance k from host FP64 fields (layout as elbm_set_fields). */
+int elbm_ensemble_set_fields(elbm_ensemble *e, int k, const double *rho, const double *u, const double *T);
+int elbm_ensemble_get_fields(elbm_ensemble *e, int k, double *rho, double *u, double *T);
+/* Schedule: persistent (optionally replayed from a CUDA graph) or one launch per
+ * instance.  Results are identical. */
+int elbm_ensemble_set_mode(elbm_ensemble *e, int mode, int use_graph);
+/* Persistent schedule: tile height (4, 8 or 16 rows of 32 nodes) and resident CTAs
+ * per SM (the grid is that times the SM count, capped by the tile count). */
+int elbm_ensemble_set_schedule(elbm_ensemble *e, int tile_y, int ctas_per_sm);
+int elbm_ensemble_get_schedule(const elbm_ensemble *e, int *tile_y, int *ctas_per_sm, int *grid);
+/* Autotuner: times every (tile height, CTAs per SM) the hardware can hold over
+ * trial_steps steps each and keeps the fastest; with use_cache, a schedule tuned
+ * before for the same store kind and size class (log2 of the node count) is reused.
+ * The candidates write only the spare store, so the state is unchanged. */
+int elbm_ensemble_tune(elbm_ensemble *e, int trial_steps, int use_cache);
+/* Advances every instance nsteps steps (asynchronous). */
+int elbm_ensemble_step(elbm_ensemble *e, int nsteps);
+/* Synchronises and returns (and clears) the latched device status. */
+int elbm_ensemble_sync(elbm_ensemble *e);
+long long elbm_ensemble_launch_count(const elbm_ensemble *e);
+long long elbm_ensemble_nodes(const elbm_ensemble *e);
+int elbm_ensemble_destroy(elbm_ensemble *e);
+
 /* Static string for a status code. */
 const char *elbm_status_str(int code);
 

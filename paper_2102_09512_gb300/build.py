@@ -70,7 +70,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir: s
             if verbose:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append((obj, cmd))
-    for name in ("elbm_api", "elbm_noalloc"):
+    for name in ("elbm_api", "elbm_noalloc", "elbm_ensemble"):
         obj = os.path.join(out_dir, f"{name}.o")
         jobs.append((obj, [exe, *ARCH, *FLAGS, *extra_flags, "-c", os.path.join(CSRC, f"{name}.cu"), "-o", obj]))
     workers = min(len(jobs), max(2, os.cpu_count() or 2))

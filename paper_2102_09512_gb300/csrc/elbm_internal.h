@@ -90,6 +90,17 @@ struct AuxLayout {
     int max_blocks;
 };
 
+// Device-side description of a D2Q9 ensemble (arrays live in the ensemble's
+// auxiliary buffer).
+constexpr int kMaxEnsemble = 1024;
+struct EnsembleArgs {
+    const KParams* params;      // [n] per-instance parameters
+    const long long* offset;    // [n] element offset of instance k in both stores
+    const int* tile_start;      // [n+1] prefix sums of the instances' tile counts
+    const int* tiles_x;         // [n] tiles per row of instance k
+    int n, ntiles;
+};
+
 // Launchers for one (lattice, store) combination.  Each returns the first CUDA
 // error it meets and adds the number of kernels it launched to *launches.
 struct Ops {
@@ -111,6 +122,9 @@ struct Ops {
                                      int* nblocks, int* status, cudaStream_t s, long long* launches);
     cudaError_t (*conservation)(const KParams& p, const void* pop, double* partials, int* nblocks,
                                 cudaStream_t s, long long* launches);
+    cudaError_t (*step_ensemble)(const EnsembleArgs& a, const void* src, void* dst, int* status, int ty,
+                                 int grid, cudaStream_t s, long long* launches);
+    int (*ensemble_occupancy)(int ty);
 };
 
 const Ops* ops_d2_f64();

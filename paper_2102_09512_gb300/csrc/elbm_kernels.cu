@@ -359,15 +359,17 @@ __device__ __forceinline__ bool halo_node(const KParams& p, int h, int x0, int y
 
 // D2Q9: one thread per node of a TX x TY tile.  Phase 1 pulls the populations into
 // registers and puts Q~ of the tile and its halo ring into shared memory; phase 2
-// collides and stores.  One launch per step, no intermediate field in HBM.
+// collides and stores.  One launch per step, no intermediate field in HBM.  The tile
+// body is shared by the per-lattice kernel and the persistent ensemble kernel;
+// `partial` (may be null) receives the tile's totals.
 template <int TY>
-__global__ void __launch_bounds__(TX * TY)
-fused2d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* __restrict__ dst,
-               double* __restrict__ partials, int* __restrict__ status) {
+__device__ __forceinline__ void fused2d_tile(const KParams& p, const P* __restrict__ src, P* __restrict__ dst,
+                                             int bx, int by, double* __restrict__ partial,
+                                             int* __restrict__ status) {
     __shared__ R qx[TY][TX + 2];
     __shared__ R qy[TY + 2][TX];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx * TX, y0 = by * TY;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < p.nx && y < p.ny;
     const int xl = min(x0 + TX, p.nx) - 1 - x0, yl = min(y0 + TY, p.ny) - 1 - y0;
@@ -412,7 +414,39 @@ fused2d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
         store_node(p, dst, node_index(p, x, y, 0), f, g);
     }
     flag_if(bad, status);
-    block_sum5(tot, partials + 5 * (blockIdx.x + gridDim.x * blockIdx.y));
+    if (partial) block_sum5(tot, partial);
+    __syncthreads();   // the shared arrays are reused by the next tile of a persistent CTA
+}
+
+template <int TY>
+__global__ void __launch_bounds__(TX * TY)
+fused2d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* __restrict__ dst,
+               double* __restrict__ partials, int* __restrict__ status) {
+    fused2d_tile<TY>(p, src, dst, blockIdx.x, blockIdx.y, partials + 5 * (blockIdx.x + gridDim.x * blockIdx.y),
+                     status);
+}
+
+// Persistent D2Q9 ensemble step: the tiles of all instances form one work list
+// (instance k owns tiles [tile_start[k], tile_start[k+1]), tiles_x[k] per row); CTA
+// b processes tiles b, b + gridDim.x, ...  Instance k's populations start at element
+// offset[k] of both stores; its parameters are params[k].  No totals are kept.
+template <int TY>
+__global__ void __launch_bounds__(TX * TY)
+ensemble2d_kernel(const EnsembleArgs a, const P* __restrict__ src, P* __restrict__ dst, int* __restrict__ status) {
+    __shared__ int s_start[kMaxEnsemble + 1];
+    __shared__ int s_tx[kMaxEnsemble];
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    for (int k = tid; k <= a.n; k += TX * TY) s_start[k] = a.tile_start[k];
+    for (int k = tid; k < a.n; k += TX * TY) s_tx[k] = a.tiles_x[k];
+    __syncthreads();
+    int k = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        while (t >= s_start[k + 1]) ++k;   // t increases, so k only moves forward
+        const int local = t - s_start[k];
+        const int bx = local % s_tx[k], by = local / s_tx[k];
+        const long long off = a.offset[k];
+        fused2d_tile<TY>(a.params[k], src + off, dst + off, bx, by, nullptr, status);
+    }
 }
 
 // Q~_zzz of the node (x, y, z) by a direct gather (used once per z segment).
@@ -789,6 +823,33 @@ cudaError_t launch_fused_reread(const KParams& p, const void* src, void* dst, do
     return launch_fused<kD>(p, src, dst, partials, nblocks, status, s, launches, true);
 }
 
+// Persistent ensemble step with tile height ty (4, 8 or 16) and `grid` CTAs.
+cudaError_t launch_ensemble(const EnsembleArgs& a, const void* src, void* dst, int* status, int ty, int grid,
+                            cudaStream_t s, long long* launches) {
+    if constexpr (kD == 2) {
+        if (ty == 4) ensemble2d_kernel<4><<<grid, dim3(TX, 4), 0, s>>>(a, (const P*)src, (P*)dst, status);
+        else if (ty == 16) ensemble2d_kernel<16><<<grid, dim3(TX, 16), 0, s>>>(a, (const P*)src, (P*)dst, status);
+        else ensemble2d_kernel<8><<<grid, dim3(TX, 8), 0, s>>>(a, (const P*)src, (P*)dst, status);
+        ++*launches;
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+// Occupancy (resident CTAs per SM) of the ensemble kernel with tile height ty.
+int ensemble_occupancy(int ty) {
+    int nb = 0;
+    if constexpr (kD == 2) {
+        cudaError_t e;
+        if (ty == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ensemble2d_kernel<4>, TX * 4, 0);
+        else if (ty == 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ensemble2d_kernel<16>, TX * 16, 0);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ensemble2d_kernel<8>, TX * 8, 0);
+        if (e != cudaSuccess) return 0;
+    }
+    return nb;
+}
+
 cudaError_t launch_totals(const KParams& p, const void* pop, double* partials, int* nblocks, cudaStream_t s,
                           long long* launches) {
     totals_kernel<<<kTotalsBlocks, kThreads, 0, s>>>(p, (const P*)pop, partials);
@@ -799,7 +860,7 @@ cudaError_t launch_totals(const KParams& p, const void* pop, double* partials, i
 
 const Ops kOps = {kD,          kST,           sizeof(P) / 2,  sizeof(R),            max_blocks,
                   launch_init, launch_fields, launch_twopass, launch_fused_default, launch_fused_reread,
-                  launch_totals};
+                  launch_totals, launch_ensemble, ensemble_occupancy};
 
 }  // namespace
 

@@ -24,6 +24,7 @@ ELBM_BC_PERIODIC, ELBM_BC_ZEROGRAD = 0, 1
 ELBM_F64, ELBM_F32, ELBM_F16DEV, ELBM_BF16DEV = 0, 1, 2, 3
 ELBM_DERIV_UPWIND, ELBM_DERIV_CENTRAL = 0, 1
 ELBM_KERNEL_FUSED, ELBM_KERNEL_TWOPASS, ELBM_KERNEL_FUSED_REREAD = 0, 1, 2
+ELBM_ENSEMBLE_PERSISTENT, ELBM_ENSEMBLE_PER_INSTANCE = 0, 1
 
 STORES = {"f64": ELBM_F64, "f32": ELBM_F32, "f16dev": ELBM_F16DEV, "bf16dev": ELBM_BF16DEV}
 VALUE_BYTES = {ELBM_F64: 8, ELBM_F32: 4, ELBM_F16DEV: 2, ELBM_BF16DEV: 2}
@@ -75,6 +76,22 @@ _SIGS = {
     "elbm_destroy": (ctypes.c_int, [_vp]),
     "elbm_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "elbm_step_noalloc": (ctypes.c_int, [ctypes.POINTER(elbm_params), _vp, _vp, _vp]),
+    "elbm_ensemble_create": (ctypes.c_int, [ctypes.POINTER(elbm_params), ctypes.c_int, ctypes.POINTER(_vp)]),
+    "elbm_ensemble_bytes_required": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t),
+                                                    ctypes.POINTER(ctypes.c_size_t)]),
+    "elbm_ensemble_bind": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "elbm_ensemble_set_fields": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "elbm_ensemble_get_fields": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "elbm_ensemble_set_mode": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "elbm_ensemble_set_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "elbm_ensemble_get_schedule": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                                  ctypes.POINTER(ctypes.c_int)]),
+    "elbm_ensemble_tune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "elbm_ensemble_step": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "elbm_ensemble_sync": (ctypes.c_int, [_vp]),
+    "elbm_ensemble_launch_count": (ctypes.c_longlong, [_vp]),
+    "elbm_ensemble_nodes": (ctypes.c_longlong, [_vp]),
+    "elbm_ensemble_destroy": (ctypes.c_int, [_vp]),
 }
 
 
@@ -204,6 +221,70 @@ def elbm_step_noalloc(params: elbm_params, src: int, dst: int, stream: int) -> i
     return lib().elbm_step_noalloc(ctypes.byref(params), src, dst, stream)
 
 
+def elbm_ensemble_create(params_list) -> int:
+    arr = (elbm_params * len(params_list))(*params_list)
+    h = _vp()
+    _check(lib().elbm_ensemble_create(arr, len(params_list), ctypes.byref(h)), "elbm_ensemble_create")
+    return h.value
+
+
+def elbm_ensemble_bytes_required(e):
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().elbm_ensemble_bytes_required(e, ctypes.byref(a), ctypes.byref(b)), "elbm_ensemble_bytes_required")
+    return a.value, b.value
+
+
+def elbm_ensemble_bind(e, pop_a, pop_b, aux, stream):
+    _check(lib().elbm_ensemble_bind(e, pop_a, pop_b, aux, stream), "elbm_ensemble_bind")
+
+
+def elbm_ensemble_set_fields(e, k, rho, u, T):
+    return lib().elbm_ensemble_set_fields(e, int(k), _ptr(rho), _ptr(u), _ptr(T))
+
+
+def elbm_ensemble_get_fields(e, k, rho, u, T):
+    return lib().elbm_ensemble_get_fields(e, int(k), _ptr(rho), _ptr(u), _ptr(T))
+
+
+def elbm_ensemble_set_mode(e, mode, use_graph=1):
+    _check(lib().elbm_ensemble_set_mode(e, int(mode), int(use_graph)), "elbm_ensemble_set_mode")
+
+
+def elbm_ensemble_set_schedule(e, tile_y, ctas_per_sm):
+    _check(lib().elbm_ensemble_set_schedule(e, int(tile_y), int(ctas_per_sm)), "elbm_ensemble_set_schedule")
+
+
+def elbm_ensemble_get_schedule(e):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().elbm_ensemble_get_schedule(e, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "elbm_ensemble_get_schedule")
+    return a.value, b.value, c.value
+
+
+def elbm_ensemble_tune(e, trial_steps=3, use_cache=0):
+    _check(lib().elbm_ensemble_tune(e, int(trial_steps), int(use_cache)), "elbm_ensemble_tune")
+
+
+def elbm_ensemble_step(e, nsteps):
+    return lib().elbm_ensemble_step(e, int(nsteps))
+
+
+def elbm_ensemble_sync(e):
+    return lib().elbm_ensemble_sync(e)
+
+
+def elbm_ensemble_launch_count(e):
+    return int(lib().elbm_ensemble_launch_count(e))
+
+
+def elbm_ensemble_nodes(e):
+    return int(lib().elbm_ensemble_nodes(e))
+
+
+def elbm_ensemble_destroy(e):
+    return lib().elbm_ensemble_destroy(e)
+
+
 # ---------------------------------------------------------------------------
 # convenience wrapper
 # ---------------------------------------------------------------------------
@@ -320,6 +401,93 @@ class Solver:
         if self.h is not None:
             elbm_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ensemble:
+    """Independent D2Q9 lattices of uneven sizes stepped together (caller-owned
+    buffers allocated with PyTorch)."""
+
+    def __init__(self, params_list, device="cuda", stream=None):
+        import torch
+
+        self.params = list(params_list)
+        self.sizes = [(p.nx, p.ny) for p in self.params]
+        self.e = elbm_ensemble_create(self.params)
+        try:
+            pop, aux = elbm_ensemble_bytes_required(self.e)
+            dev = torch.device(device)
+            self.pop_a = torch.empty(pop, dtype=torch.uint8, device=dev)
+            self.pop_b = torch.empty(pop, dtype=torch.uint8, device=dev)
+            self.aux = torch.empty(aux, dtype=torch.uint8, device=dev)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+            elbm_ensemble_bind(self.e, self.pop_a.data_ptr(), self.pop_b.data_ptr(), self.aux.data_ptr(),
+                               self.stream.cuda_stream)
+        except Exception:
+            elbm_ensemble_destroy(self.e)
+            self.e = None
+            raise
+
+    @classmethod
+    def from_cases(cls, cases, store="f32", **kw):
+        ps = []
+        for c in cases:
+            ps.append(make_params(2, c.nx, c.ny, 1, c.gamma, c.Pr, c.mu0, c.T0, c.mu_exp, c.bc, store, 0,
+                                  float(np.mean(c.rho)), float(np.mean(c.T))))
+        ens = cls(ps, **kw)
+        for k, c in enumerate(cases):
+            ens.set_fields(k, c.rho, c.u, c.T)
+        return ens
+
+    def set_fields(self, k, rho, u, T):
+        nx, ny = self.sizes[k]
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(nx * ny)
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(2 * nx * ny)
+        T = np.ascontiguousarray(T, dtype=np.float64).reshape(nx * ny)
+        _check(elbm_ensemble_set_fields(self.e, k, rho, u, T), "elbm_ensemble_set_fields")
+
+    def fields(self, k):
+        nx, ny = self.sizes[k]
+        rho, u, T = np.empty(nx * ny), np.empty((2, nx * ny)), np.empty(nx * ny)
+        _check(elbm_ensemble_get_fields(self.e, k, rho, u, T), "elbm_ensemble_get_fields")
+        return rho, u, T
+
+    def set_mode(self, mode, use_graph=True):
+        elbm_ensemble_set_mode(self.e, mode, 1 if use_graph else 0)
+
+    def set_schedule(self, tile_y, ctas_per_sm):
+        elbm_ensemble_set_schedule(self.e, tile_y, ctas_per_sm)
+
+    def schedule(self):
+        return elbm_ensemble_get_schedule(self.e)
+
+    def tune(self, trial_steps=3, use_cache=False):
+        elbm_ensemble_tune(self.e, trial_steps, 1 if use_cache else 0)
+        return self.schedule()
+
+    def step(self, n=1):
+        _check(elbm_ensemble_step(self.e, n), "elbm_ensemble_step")
+
+    def sync(self):
+        _check(elbm_ensemble_sync(self.e), "elbm_ensemble_sync")
+
+    @property
+    def nodes(self):
+        return elbm_ensemble_nodes(self.e)
+
+    @property
+    def launches(self):
+        return elbm_ensemble_launch_count(self.e)
+
+    def close(self):
+        if self.e is not None:
+            elbm_ensemble_destroy(self.e)
+            self.e = None
 
     def __del__(self):
         try:

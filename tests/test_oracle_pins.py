@@ -535,7 +535,7 @@ def test_standing_normal_shock_rankine_hugoniot():
     assert r_rho == pytest.approx(gold["rho2_over_rho1"], abs=6e-5)
     assert r_T == pytest.approx(gold["T2_over_T1"], abs=6e-5)
     nx, ny = 300, 2
-    c = C.shock_vortex(nx=nx, ny=ny, Ma_s=1.2, Ma_v=0.0, r_v=nx / 16.0, Re=150.0, Pr=0.75)
+    c = C.shock_vortex(nx=nx, ny=ny, Ma_s=1.2, Ma_v=0.0, r_v=nx / 16.0, Re=150.0, Pr=0.75, r_v_mu=nx / 16.0)
     p = params_of(c)
     s = O.init(p, c.rho, c.u, c.T)
     O.step(s, 1500)
