@@ -258,6 +258,37 @@ def time_e2e(E, torch, case, store, steps, stream):
     return 1e3 * el / steps, h2d, d2h
 
 
+def ensemble_measure(E, torch, steps, store="f32"):
+    """Batched ensemble of 64 uneven D2Q9 instances (Sod tubes and shock-vortex cases,
+    sides 256..1024, Ma_s ~ U[1.1, 1.5]): one persistent autotuned launch per step
+    replayed from a CUDA graph, against one launch per instance."""
+    from paper_2102_09512_gb300 import cases as C
+    specs = C.ensemble(64)
+    cases = [C.build_instance(s) for s in specs]
+    ens = E.Ensemble.from_cases(cases, store=store)
+    ty, ctas, grid = ens.tune(trial_steps=3)
+    out = {"instances": len(cases), "nodes": ens.nodes, "store": store,
+           "schedule": {"tile": [32, ty], "ctas_per_sm": ctas, "grid": grid}}
+    for name, mode, graph in (("persistent_graph", 0, True), ("per_instance", 1, False)):
+        ens.set_mode(mode, graph)
+        ens.step(3)
+        ens.sync()
+        l0 = ens.launches
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(ens.stream)
+        ens.step(steps)
+        e1.record(ens.stream)
+        e1.synchronize()
+        ens.sync()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_step": ms, "glups": ens.nodes / (ms * 1e-3) / 1e9,
+                     "launches_per_step": (ens.launches - l0) / steps}
+    out["speedup_persistent_vs_per_instance"] = out["per_instance"]["ms_per_step"] / out["persistent_graph"]["ms_per_step"]
+    ens.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -267,6 +298,7 @@ def main():
     ap.add_argument("--stores", default="f32,f16dev,bf16dev,f64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--size", type=int, default=N_SIDE, help="box side (the bench workload is 256)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -350,6 +382,10 @@ def main():
         e2e = {"value": ws * case.N / (e2e_ms * 1e-3) / 1e9, "unit": "GLUPS", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
 
+    ens = None
+    if not args.no_ensemble:
+        ens = ensemble_measure(E, torch, args.steps)
+
     cpu = None
     if not args.no_cpu_baseline:
         v, cores, sample = cpu_oracle_sample()
@@ -370,7 +406,7 @@ def main():
                    "schedule": "fused", "l2": "inputs larger than L2 (3.6 GB FP32 store)",
                    "parallelism": "replicas" if ws > 1 else "single-gpu"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_head,
-        "clocks": clocks, "variants": variants,
+        "clocks": clocks, "variants": variants, "ensemble": ens,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:

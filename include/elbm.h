@@ -137,7 +137,8 @@ int elbm_step_totals(elbm_handle *h, double out[5]);
 int elbm_set_kernel(elbm_handle *h, int kernel);
 
 /* Length of the z segment each CTA of the fused D3Q27 kernel marches over
- * (default min(nz, 32)); a tuning knob, results do not depend on it. */
+ * (default min(nz, 64) for FP32 stores, min(nz, 32) otherwise); a tuning knob,
+ * results agree to rounding. */
 int elbm_set_tile_z(elbm_handle *h, int tz);
 
 /* Raw copy of the current population store (pop_bytes) to or from host memory,

@@ -47,7 +47,10 @@ inline int fill_kparams(const elbm_params& p, KParams& k, int* D_out) {
     k.T0 = p.T0;
     k.mu_exp = p.mu_exp;
     k.deriv = p.deriv;
-    k.tz = p.nz < 32 ? p.nz : 32;
+    // z segment of the fused D3Q27 kernels: longer for FP32 (one CTA per SM, so
+    // fewer prologues per plane matter more), measured at 256^3
+    const int tz = p.store == ELBM_F32 ? 64 : 32;
+    k.tz = p.nz < tz ? p.nz : tz;
     if (dev) {
         // Rest state f^eq(rho_ref, 0, T_ref), g^eq(rho_ref, 0, T_ref): with u = 0 the
         // per-axis factors are phi = (T/2, 1-T, T/2) and psi = (T^2/2, -T^2, T^2/2).
