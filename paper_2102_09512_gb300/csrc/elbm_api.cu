@@ -56,22 +56,21 @@ const Ops* pick_ops(int D, int store) {
     return nullptr;
 }
 
-__global__ void finalize_kernel(const double* __restrict__ partials, int nb, double* __restrict__ out) {
-    double s[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0};
+// Compensated FP64 sum over nb partial vectors of `width` values (width <= 8).
+__global__ void finalize_kernel(const double* __restrict__ partials, int nb, int width, double* __restrict__ out) {
+    double s[8] = {0, 0, 0, 0, 0, 0, 0, 0}, c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {   // Neumaier
-            const double v = partials[5 * j + k];
+        for (int k = 0; k < width; ++k) {   // Neumaier
+            const double v = partials[(size_t)width * j + k];
             const double t = s[k] + v;
             c[k] += fabs(s[k]) >= fabs(v) ? (s[k] - t) + v : (v - t) + s[k];
             s[k] = t;
         }
     }
-    __shared__ double red[5][256];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) red[k][threadIdx.x] = s[k] + c[k];
+    __shared__ double red[8][256];
+    for (int k = 0; k < width; ++k) red[k][threadIdx.x] = s[k] + c[k];
     __syncthreads();
-    if (threadIdx.x < 5) {   // fixed-order compensated sum of the 256 thread values
+    if (threadIdx.x < width) {   // fixed-order compensated sum of the 256 thread values
         const int k = threadIdx.x;
         double ss = 0.0, cc = 0.0;
         for (int j = 0; j < 256; ++j) {
@@ -89,6 +88,7 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? ELBM_OK : ELBM_ERR_CU
 int* status_ptr(elbm_handle* h) { return (int*)(h->auxp + h->aux.status); }
 double* totals_ptr(elbm_handle* h) { return (double*)(h->auxp + h->aux.totals); }
 double* step_partials(elbm_handle* h) { return (double*)(h->auxp + h->aux.partials); }
+// query partials hold up to 8 values per CTA (turbulence statistics)
 double* query_partials(elbm_handle* h) {
     return (double*)(h->auxp + h->aux.partials) + 5 * (size_t)h->aux.max_blocks;
 }
@@ -109,12 +109,12 @@ int sync_status(elbm_handle* h) {
     return ELBM_OK;
 }
 
-int finalize_to_host(elbm_handle* h, const double* partials, int nb, double out[5]) {
-    finalize_kernel<<<1, 256, 0, h->stream>>>(partials, nb, totals_ptr(h));
+int finalize_to_host(elbm_handle* h, const double* partials, int nb, double* out, int width = 5) {
+    finalize_kernel<<<1, 256, 0, h->stream>>>(partials, nb, width, totals_ptr(h));
     ++h->launches;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(out, totals_ptr(h), 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        e = cudaMemcpyAsync(out, totals_ptr(h), width * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return ELBM_ERR_CUDA;
     return sync_status(h);
 }
@@ -155,7 +155,7 @@ int elbm_create(const elbm_params* prm, elbm_handle** out) {
     a.totals = off;
     off = align_up(off + 8 * sizeof(double));
     a.partials = off;
-    off = align_up(off + 2 * 5 * sizeof(double) * (size_t)a.max_blocks);
+    off = align_up(off + (5 + 8) * sizeof(double) * (size_t)a.max_blocks);
     a.qfield = off;
     off = align_up(off + (size_t)D * N * h->ops->real_bytes);
     a.staging = off;
@@ -255,6 +255,28 @@ int elbm_conservation(elbm_handle* h, double out[5]) {
     cudaError_t e = h->ops->conservation(h->kp, h->pop[h->cur], query_partials(h), &nb, h->stream, &h->launches);
     if (e != cudaSuccess) return ELBM_ERR_CUDA;
     return finalize_to_host(h, query_partials(h), nb, out);
+}
+
+int elbm_turbulence_stats(elbm_handle* h, double out[8]) {
+    if (!h || !h->bound || !out) return ELBM_ERR_ARG;
+    int nb = 0;
+    double* part = query_partials(h);   // 8 values x (<= max_blocks) CTAs
+    cudaError_t e = h->ops->stats(h->kp, h->pop[h->cur], part, &nb, h->stream, &h->launches);
+    if (e != cudaSuccess) return ELBM_ERR_CUDA;
+    double sums[8];
+    const int rc = finalize_to_host(h, part, nb, sums, 8);
+    if (rc != ELBM_OK) return rc;
+    const double N = (double)h->N;
+    const double mrho = sums[0] / N, mT = sums[5] / N;
+    out[0] = mrho;                                               // <rho>
+    out[1] = std::sqrt(std::fmax(sums[1] / N - mrho * mrho, 0.0));   // rho_rms
+    out[2] = 0.5 * sums[2] / N;                                  // K = <rho u.u>/2
+    out[3] = std::sqrt(sums[3] / N / h->D);                      // u_rms = sqrt(<u.u>/D)
+    out[4] = std::sqrt(sums[4] / N);                             // theta_rms
+    out[5] = mT;                                                 // <T>
+    out[6] = std::sqrt(std::fmax(sums[6] / N - mT * mT, 0.0));   // T_rms
+    out[7] = sums[7] / N;                                        // <(d u_x/d x)^2>
+    return ELBM_OK;
 }
 
 int elbm_step_totals(elbm_handle* h, double out[5]) {

@@ -128,6 +128,8 @@ struct Ops {
     cudaError_t (*step_ensemble)(const EnsembleArgs& a, const void* src, void* dst, int* status, int ty,
                                  int grid, cudaStream_t s, long long* launches);
     int (*ensemble_occupancy)(int ty);
+    cudaError_t (*stats)(const KParams& p, const void* pop, double* partials, int* nblocks, cudaStream_t s,
+                         long long* launches);   // 8 partial sums per CTA
 };
 
 const Ops* ops_d2_f64();

@@ -260,6 +260,79 @@ __global__ void totals_kernel(const __grid_constant__ KParams p, const P* __rest
     block_sum5(s, partials + 5 * blockIdx.x);
 }
 
+// Velocity of node n from its f values only (rho and rho u).
+__device__ __forceinline__ void node_velocity(const KParams& p, const P* __restrict__ pop, long long n, R u[3]) {
+    R rho = 0, j[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        R f, g;
+        Cd::dec(pop[(size_t)i * (size_t)p.N + (size_t)n], f, g);
+        rho += f;
+        if (cx_of(i)) j[0] += cx_of(i) * f;
+        if (cy_of(i)) j[1] += cy_of(i) * f;
+        if (cz_of<kD>(i)) j[2] += cz_of<kD>(i) * f;
+    }
+    if constexpr (DEV) rho += R(p.rest_rho);
+    const R inv = qdiv(R(1), rho);
+    u[0] = j[0] * inv;
+    u[1] = j[1] * inv;
+    u[2] = j[2] * inv;
+}
+
+// Turbulence statistics of the current state (one FP64 partial vector per CTA):
+// sums of rho, rho^2, rho u.u, u.u, theta^2, T, T^2 and (d u_x / d x)^2 with the
+// dilatation theta = div u and d u_x / d x by second-order central differences
+// (boundary nodes use the ghost values of the boundary map).
+constexpr int kStats = 8;
+__global__ void stats_kernel(const __grid_constant__ KParams p, const P* __restrict__ pop,
+                             double* __restrict__ partials) {
+    double acc[kStats] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < p.N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((long long)p.nx * p.ny));
+        R f[Q], g[Q];
+        load_local(p, pop, n, f, g);
+        Moments<R> m;
+        node_moments<kD, R, false, DEV>(f, g, p, m);
+        R up[3], um[3];
+        node_velocity(p, pop, node_index(p, map_axis(x + 1, p.nx, p.per_x), y, z), up);
+        node_velocity(p, pop, node_index(p, map_axis(x - 1, p.nx, p.per_x), y, z), um);
+        const double dux = 0.5 * ((double)up[0] - (double)um[0]);
+        double theta = dux;
+        node_velocity(p, pop, node_index(p, x, map_axis(y + 1, p.ny, p.per_y), z), up);
+        node_velocity(p, pop, node_index(p, x, map_axis(y - 1, p.ny, p.per_y), z), um);
+        theta += 0.5 * ((double)up[1] - (double)um[1]);
+        if (kD == 3) {
+            node_velocity(p, pop, node_index(p, x, y, map_axis(z + 1, p.nz, p.per_z)), up);
+            node_velocity(p, pop, node_index(p, x, y, map_axis(z - 1, p.nz, p.per_z)), um);
+            theta += 0.5 * ((double)up[2] - (double)um[2]);
+        }
+        const double rho = m.rho, T = m.T;
+        const double uu = (double)m.ux * m.ux + (double)m.uy * m.uy + (double)m.uz * m.uz;
+        acc[0] += rho;
+        acc[1] += rho * rho;
+        acc[2] += rho * uu;
+        acc[3] += uu;
+        acc[4] += theta * theta;
+        acc[5] += T;
+        acc[6] += T * T;
+        acc[7] += dux * dux;
+    }
+    // block reduction of kStats values (two passes of the 5-value reduction)
+    double a5[5] = {acc[0], acc[1], acc[2], acc[3], acc[4]};
+    block_sum5(a5, partials + (size_t)kStats * blockIdx.x);
+    __syncthreads();
+    double b5[5] = {acc[5], acc[6], acc[7], 0.0, 0.0};
+    __shared__ double tail[5];
+    block_sum5(b5, tail);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        partials[(size_t)kStats * blockIdx.x + 5] = tail[0];
+        partials[(size_t)kStats * blockIdx.x + 6] = tail[1];
+        partials[(size_t)kStats * blockIdx.x + 7] = tail[2];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // two-pass schedule
 // ---------------------------------------------------------------------------
@@ -850,6 +923,14 @@ int ensemble_occupancy(int ty) {
     return nb;
 }
 
+cudaError_t launch_stats(const KParams& p, const void* pop, double* partials, int* nblocks, cudaStream_t s,
+                         long long* launches) {
+    stats_kernel<<<kTotalsBlocks, kThreads, 0, s>>>(p, (const P*)pop, partials);
+    ++*launches;
+    *nblocks = kTotalsBlocks;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_totals(const KParams& p, const void* pop, double* partials, int* nblocks, cudaStream_t s,
                           long long* launches) {
     totals_kernel<<<kTotalsBlocks, kThreads, 0, s>>>(p, (const P*)pop, partials);
@@ -860,7 +941,7 @@ cudaError_t launch_totals(const KParams& p, const void* pop, double* partials, i
 
 const Ops kOps = {kD,          kST,           sizeof(P) / 2,  sizeof(R),            max_blocks,
                   launch_init, launch_fields, launch_twopass, launch_fused_default, launch_fused_reread,
-                  launch_totals, launch_ensemble, ensemble_occupancy};
+                  launch_totals, launch_ensemble, ensemble_occupancy, launch_stats};
 
 }  // namespace
 

@@ -65,6 +65,7 @@ _SIGS = {
     "elbm_get_fields_device": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "elbm_conservation": (ctypes.c_int, [_vp, _dp]),
     "elbm_step_totals": (ctypes.c_int, [_vp, _dp]),
+    "elbm_turbulence_stats": (ctypes.c_int, [_vp, _dp]),
     "elbm_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int]),
     "elbm_set_tile_z": (ctypes.c_int, [_vp, ctypes.c_int]),
     "elbm_get_populations": (ctypes.c_int, [_vp, _vp]),
@@ -176,6 +177,15 @@ def elbm_step_totals(h) -> np.ndarray:
     out = np.zeros(5)
     _check(lib().elbm_step_totals(h, out.ctypes.data_as(_dp)), "elbm_step_totals")
     return out
+
+
+STATS_KEYS = ("rho_mean", "rho_rms", "K", "u_rms", "theta_rms", "T_mean", "T_rms", "dudx2")
+
+
+def elbm_turbulence_stats(h) -> dict:
+    out = np.zeros(8)
+    _check(lib().elbm_turbulence_stats(h, out.ctypes.data_as(_dp)), "elbm_turbulence_stats")
+    return dict(zip(STATS_KEYS, out.tolist()))
 
 
 def elbm_set_kernel(h, kernel: int):
@@ -370,6 +380,9 @@ class Solver:
 
     def step_totals(self) -> np.ndarray:
         return elbm_step_totals(self.h)
+
+    def turbulence_stats(self) -> dict:
+        return elbm_turbulence_stats(self.h)
 
     def set_kernel(self, k: int):
         elbm_set_kernel(self.h, k)
