@@ -536,16 +536,18 @@ __device__ __forceinline__ R direct_anomaly_z(const KParams& p, const P* __restr
 // D3Q27, pipelined.  A CTA owns a TX x TY column of nodes and marches along z over a
 // segment of p.tz planes.  For every plane q it needs the pulled pairs of its TX*TY
 // nodes and of the 2TX+2TY halo nodes; these are copied with cp.async into one of
-// NB shared-memory plane buffers, laid out [direction][slot] so that each thread
-// reads its own slot (conflict-free).  Per plane z:
-//   [A] wait for plane z+1, barrier; (NB = 3: prefetch plane z+2 into the buffer of
-//       plane z-1);
+// two shared-memory plane buffers, laid out [direction][slot].  Thread t copies and
+// reads only its own slots (its node, and halo node t for t < 2TX+2TY), so the
+// population buffers need no barrier: each thread waits for its own copies.  Only
+// the Q~ arrays (double-buffered by plane parity) are shared, and one barrier per
+// plane orders both of their hazards.  Per plane z:
+//   wait for this thread's copies of plane z+1; barrier;
 //   moments of plane z+1 (tile and halo) -> Q~ in shared memory, moments kept in
 //       registers for the next iteration;
-//   [B] barrier; read the pairs of plane z from shared memory;
-//   (NB = 2: [C] barrier, prefetch plane z+2 into the buffer of plane z);
-//   collide plane z (moments from the previous iteration, Q~ neighbours from shared
-//       memory and the rolling Q~_zzz registers) and store.
+//   read the pairs of plane z from shared memory, prefetch plane z+2 into the same
+//       slots;
+//   collide plane z (moments and Q~ from the previous iteration, the rolling Q~_zzz
+//       registers) and store.
 // Every population leaves HBM once per step; the collision overlaps the prefetch.
 template <int TY, int NB>
 struct Pipe {
@@ -567,6 +569,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* __restrict__ dst,
                double* __restrict__ partials, int* __restrict__ status) {
     using PP = Pipe<TY, NB>;
+    static_assert(NB == 2, "plane z+2 is prefetched into the slots of plane z");
     constexpr int NT = PP::NT, NH = PP::NH, NS = PP::NS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     P* buf = reinterpret_cast<P*>(smem_raw);                       // [NB][Q][NS]
@@ -644,8 +647,7 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
         const int sn = (k + 1) % NB;        // ... of plane z+1
         const bool last = (z + 1 == ze);
         cp_async_wait_all();
-        __syncthreads();                                                     // [A]
-        if (NB == 3 && z + 2 <= ze) issue_plane(map_axis(z + 2, p.nz, p.per_z), (k + 2) % NB, z + 2 < ze);
+        __syncthreads();
 
         if (active) {
             slot_moments(sn, tid, m_next);
@@ -661,7 +663,6 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
             if (haxis == 1) QY(bq ^ 1, hsy, hsx) = anomaly(hm.rho, hm.uy, hm.T);
             else QX(bq ^ 1, hsy, hsx) = anomaly(hm.rho, hm.ux, hm.T);
         }
-        __syncthreads();                                                     // [B]
 
         R f[Q], g[Q];
         if (active) {
@@ -669,10 +670,7 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
 #pragma unroll
             for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], f[i], g[i]);
         }
-        if (NB == 2) {
-            __syncthreads();                                                 // [C]
-            if (z + 2 <= ze) issue_plane(map_axis(z + 2, p.nz, p.per_z), sz, z + 2 < ze);
-        }
+        if (z + 2 <= ze) issue_plane(map_axis(z + 2, p.nz, p.per_z), sz, z + 2 < ze);
         if (active) {
             bad |= nonphysical(m_cur);
             const R Dx = dQ(p.deriv, m_cur.ux, QX(bq, ty, tx), QX(bq, ty, tx + 1), QX(bq, ty, tx + 2));
