@@ -51,8 +51,10 @@ __device__ __forceinline__ long long node_index(const KParams& p, int x, int y, 
 
 // Source nodes of the pull at node (x, y, z): direction i = a + 3b + 9c is read at
 // (xs[a], ys[b], zs[c]) = (x - c_x, y - c_y, z - c_z) with ghosts resolved by map_axis.
+// Node indices fit in 32 bits (N <= 2^31); only the per-direction plane offset
+// i * N needs 64 bits, and it is the same for every thread.
 struct PullRows {
-    long long row[3][3];   // node index of (0, ys[b], zs[c])
+    int row[3][3];   // node index of (0, ys[b], zs[c])
     int xs[3];
 };
 
@@ -73,18 +75,19 @@ __device__ __forceinline__ void pull_rows(const KParams& p, int x, int y, int z,
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int b = 0; b < 3; ++b)
-            r.row[b][c] = (long long)p.nx * ((long long)ys[b] + (long long)p.ny * (long long)zs[c]);
+            r.row[b][c] = p.nx * (ys[b] + p.ny * zs[c]);
 }
 
-__device__ __forceinline__ size_t src_elem(const KParams& p, const PullRows& r, int i) {
+// Address of the pair of direction i pulled by node r in store s.
+__device__ __forceinline__ const P* src_ptr(const KParams& p, const P* __restrict__ s, const PullRows& r, int i) {
     const int a = i % 3, b = (i / 3) % 3, c = (kD == 3) ? i / 9 : 1;
-    return (size_t)i * (size_t)p.N + (size_t)(r.row[b][c] + r.xs[a]);
+    return (s + (size_t)i * (size_t)p.N) + (unsigned)(r.row[b][c] + r.xs[a]);
 }
 
 __device__ __forceinline__ void gather(const KParams& p, const P* __restrict__ src, const PullRows& r,
                                        R* f, R* g) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) Cd::dec(src[src_elem(p, r, i)], f[i], g[i]);
+    for (int i = 0; i < Q; ++i) Cd::dec(*src_ptr(p, src, r, i), f[i], g[i]);
 }
 
 __device__ __forceinline__ void load_local(const KParams& p, const P* __restrict__ pop, long long n, R* f,
@@ -96,9 +99,9 @@ __device__ __forceinline__ void load_local(const KParams& p, const P* __restrict
 
 __device__ __forceinline__ void store_node(const KParams& p, P* __restrict__ dst, long long n, const R* f,
                                            const R* g) {
+    const unsigned nn = (unsigned)n;
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-        dst[(size_t)i * (size_t)p.N + (size_t)n] = Cd::enc(f[i], g[i]);
+    for (int i = 0; i < Q; ++i) (dst + (size_t)i * (size_t)p.N)[nn] = Cd::enc(f[i], g[i]);
 }
 
 // Totals of one node: rho, rho u_x, rho u_y, rho u_z, rho E.
@@ -596,13 +599,13 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
             PullRows r;
             pull_rows(p, x, y, q, r);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) cp_async<sizeof(P)>(bb + i * NS + tid, src + src_elem(p, r, i));
+            for (int i = 0; i < Q; ++i) cp_async<sizeof(P)>(bb + i * NS + tid, src_ptr(p, src, r, i));
         }
         if (with_halo && has_halo) {
             PullRows r;
             pull_rows(p, hx, hy, q, r);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) cp_async<sizeof(P)>(bb + i * NS + NT + tid, src + src_elem(p, r, i));
+            for (int i = 0; i < Q; ++i) cp_async<sizeof(P)>(bb + i * NS + NT + tid, src_ptr(p, src, r, i));
         }
         cp_async_commit();
     };
