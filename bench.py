@@ -143,6 +143,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def replica_time(ms, ws, device):
+    """Max over the replicas of the per-rank step time (every rank calls this, a rank
+    whose run failed passes inf so the collective still matches)."""
+    if ws == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, ws, ms_max):
+    """Whole-job throughput: the units all replicas processed over the slowest time."""
+    return ws * units_per_rank / (ms_max * 1e-3)
+
+
 def cpu_oracle_sample(min_seconds=10.0, max_seconds=30.0):
     """The FP64 oracle on the host cores on a 32^3 box of the same generator; returns
     (GLUPS, threads, description)."""
@@ -347,20 +364,21 @@ def main():
                 sampler.stop()
             print(f"bench: store {store} failed: {err}", file=sys.stderr, flush=True)
             variants[store] = {"error": str(err)}
+            replica_time(float("inf"), ws, "cuda")
             torch.cuda.synchronize()
             torch.cuda.empty_cache()
             continue
         if sampler:
             clocks = sampler.stop()
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = replica_time(ms, ws, "cuda")
         totals = g.conservation()
         g.close()
         del g
         torch.cuda.empty_cache()
-        glups = ws * case.N / (ms * 1e-3) / 1e9
+        if ms == float("inf"):
+            variants[store] = {"error": "failed on another replica"}
+            continue
+        glups = aggregate_rate(case.N, ws, ms) / 1e9
         per_gpu_gbs = case.N / (ms * 1e-3) * BYTES_PER_UPDATE[store] / 1e9
         variants[store] = {"glups": glups, "ms_per_step": ms, "timed_steps": k,
                            "algorithmic_GBs_per_gpu": per_gpu_gbs,
