@@ -47,6 +47,15 @@ inline int fill_kparams(const elbm_params& p, KParams& k, int* D_out) {
     k.T0 = p.T0;
     k.mu_exp = p.mu_exp;
     k.deriv = p.deriv;
+    k.powlaw = p.mu_exp != 0.0;
+    k.d_Cv = 1.0 / (p.gamma - 1.0);
+    k.d_invT0 = 1.0 / p.T0;
+    k.f_gm1 = (float)k.gm1;
+    k.f_Cv = (float)k.d_Cv;
+    k.f_Pr = (float)p.Pr;
+    k.f_mu0 = (float)p.mu0;
+    k.f_invT0 = (float)k.d_invT0;
+    k.f_mu_exp = (float)p.mu_exp;
     // z segment of the fused D3Q27 kernels: longer for FP32 (one CTA per SM, so
     // fewer prologues per plane matter more), measured at 256^3
     const int tz = p.store == ELBM_F32 ? 64 : 32;

@@ -21,6 +21,8 @@
 // (ping-pong), so every store is coalesced and no two threads write one element.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "elbm_internal.h"
 #include "elbm_node.cuh"
 
@@ -196,7 +198,7 @@ __global__ void init_kernel(const __grid_constant__ KParams p, const double* __r
         bad = !(r > R(0)) || !(t > R(0)) || !isfinite(r) || !isfinite(t) || !isfinite(ux) ||
               !isfinite(uy) || !isfinite(uz);
         R f[Q], g[Q];
-        equilibria<kD, R>(r, ux, uy, uz, t, R(1) / R(p.gm1), f, g);
+        equilibria<kD, R>(r, ux, uy, uz, t, par<R>(p.d_Cv, p.f_Cv), f, g);
         if constexpr (DEV) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -567,7 +569,7 @@ struct PipeBytes {
     static constexpr size_t value = Pipe<TY, NB>::smem_bytes;
 };
 
-template <int TY, int NB, int MINB>
+template <int TY, int NB, int MINB, bool EARLY>
 __global__ void __launch_bounds__(TX * TY, MINB)
 fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* __restrict__ dst,
                double* __restrict__ partials, int* __restrict__ status) {
@@ -609,14 +611,17 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
         }
         cp_async_commit();
     };
-    // moments of the node in slot `slot` of buffer sb
-    auto slot_moments = [&](int sb, int slot, Moments<R>& m) {
+    // moments of the node in slot `slot` of buffer sb (the pressure tensor only for
+    // tile nodes: halo nodes contribute Q~ alone)
+    auto slot_moments = [&](int sb, int slot, Moments<R>& m, auto full) {
         const P* bb = buf + (size_t)sb * Q * NS + slot;
         R f[Q], g[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], f[i], g[i]);
-        node_moments<kD, R, true, DEV>(f, g, p, m);
+        node_moments<kD, R, decltype(full)::value, DEV>(f, g, p, m);
     };
+    using Full = std::true_type;
+    using Lite = std::false_type;
 
     Acc5 acc;
     acc.zero();
@@ -631,14 +636,14 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     __syncthreads();
     if (active) {
-        slot_moments(0, tid, m_cur);
+        slot_moments(0, tid, m_cur, Full());
         QX(0, ty, tx + 1) = anomaly(m_cur.rho, m_cur.ux, m_cur.T);
         QY(0, ty + 1, tx) = anomaly(m_cur.rho, m_cur.uy, m_cur.T);
         qz_cur = anomaly(m_cur.rho, m_cur.uz, m_cur.T);
     }
     if (has_halo) {
         Moments<R> hm;
-        slot_moments(0, NT + tid, hm);
+        slot_moments(0, NT + tid, hm, Lite());
         if (haxis == 1) QY(0, hsy, hsx) = anomaly(hm.rho, hm.uy, hm.T);
         else QX(0, hsy, hsx) = anomaly(hm.rho, hm.ux, hm.T);
     }
@@ -652,8 +657,21 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
         cp_async_wait_all();
         __syncthreads();
 
+        // EARLY: plane z is read into registers and plane z+2 requested before the
+        // moments of plane z+1, so the copy overlaps them too (both planes are live
+        // in registers meanwhile, which only a one-CTA-per-SM launch affords)
+        R f[Q], g[Q];
+        if (EARLY) {
+            if (active) {
+                const P* bb = buf + (size_t)sz * Q * NS + tid;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], f[i], g[i]);
+            }
+            if (z + 2 <= ze) issue_plane(map_axis(z + 2, p.nz, p.per_z), sz, z + 2 < ze);
+        }
+
         if (active) {
-            slot_moments(sn, tid, m_next);
+            slot_moments(sn, tid, m_next, Full());
             qz_next = anomaly(m_next.rho, m_next.uz, m_next.T);
             if (!last) {
                 QX(bq ^ 1, ty, tx + 1) = anomaly(m_next.rho, m_next.ux, m_next.T);
@@ -662,18 +680,19 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
         }
         if (!last && has_halo) {
             Moments<R> hm;
-            slot_moments(sn, NT + tid, hm);
+            slot_moments(sn, NT + tid, hm, Lite());
             if (haxis == 1) QY(bq ^ 1, hsy, hsx) = anomaly(hm.rho, hm.uy, hm.T);
             else QX(bq ^ 1, hsy, hsx) = anomaly(hm.rho, hm.ux, hm.T);
         }
 
-        R f[Q], g[Q];
-        if (active) {
-            const P* bb = buf + (size_t)sz * Q * NS + tid;
+        if (!EARLY) {
+            if (active) {
+                const P* bb = buf + (size_t)sz * Q * NS + tid;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], f[i], g[i]);
+                for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], f[i], g[i]);
+            }
+            if (z + 2 <= ze) issue_plane(map_axis(z + 2, p.nz, p.per_z), sz, z + 2 < ze);
         }
-        if (z + 2 <= ze) issue_plane(map_axis(z + 2, p.nz, p.per_z), sz, z + 2 < ze);
         if (active) {
             bad |= nonphysical(m_cur);
             const R Dx = dQ(p.deriv, m_cur.ux, QX(bq, ty, tx), QX(bq, ty, tx + 1), QX(bq, ty, tx + 2));
@@ -794,7 +813,9 @@ constexpr int kTotalsBlocks = 2 * 152;   // totals_kernel grid (grid-stride)
 // Pipelined D3Q27 kernel per store: two plane buffers.  FP32 pairs make them 145 KB
 // (one CTA per SM, up to 255 registers; a third buffer would leave L1 almost no
 // room and measured 35 % slower); FP16/BF16 pairs are half the size (two CTAs per
-// SM); FP64 uses the re-read kernel (its plane buffers would not fit).
+// SM); FP64 uses the re-read kernel (its plane buffers would not fit).  With one CTA
+// per SM the registers also hold plane z while plane z+1's moments are computed, so
+// the prefetch of plane z+2 starts one phase earlier (EARLY; 10 % faster at 256^3).
 #ifndef ELBM_PIPE_NB_F32
 #define ELBM_PIPE_NB_F32 2
 #endif
@@ -805,6 +826,10 @@ constexpr bool kPipe = (kST != ST_F64);
 constexpr int kNB = (kST == ST_F32) ? ELBM_PIPE_NB_F32 : ELBM_PIPE_NB_F16;
 constexpr int kMinB = (PipeBytes<kTY3, kNB>::value * 2 + 2048 <= 228 * 1024) ? 2 : 1;
 using PipeCfg = Pipe<kTY3, kNB>;
+#ifndef ELBM_EARLY
+#define ELBM_EARLY 1
+#endif
+constexpr bool kEarly = ELBM_EARLY && kMinB == 1;
 
 inline unsigned blocks_1d(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
@@ -867,7 +892,7 @@ cudaError_t launch_fused(const KParams& p, const void* src, void* dst, double* p
         bool launched = false;
         if constexpr (kPipe) {
             if (!reread) {
-                auto kern = fused3d_kernel<kTY3, kNB, kMinB>;
+                auto kern = fused3d_kernel<kTY3, kNB, kMinB, kEarly>;
                 // the dynamic shared-memory limit is a per-function attribute; setting it
                 // again is cheap and keeps this correct for every device of the process
                 cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

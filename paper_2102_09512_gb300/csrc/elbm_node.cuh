@@ -33,7 +33,17 @@ struct KParams {
     int tz;                      // z-segment length of the fused 3D kernels
     float rest32[54];            // rest-state populations (f then g) of the deviation stores
     float rest_rho, rest_Pxx, rest_Pyy, rest_Pzz, rest_E;   // their moment sums
+    // The same parameters precomputed in both arithmetic types, so that no kernel
+    // converts or divides a double per node (the FP64 pipe of GB300 is narrow).
+    int powlaw;                                            // mu_exp != 0
+    double d_Cv, d_invT0;
+    float f_gm1, f_Cv, f_Pr, f_mu0, f_invT0, f_mu_exp;
 };
+
+// Parameter in the arithmetic type R.
+template <typename R> __device__ __forceinline__ R par(double d, float f);
+template <> __device__ __forceinline__ double par<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float par<float>(double, float f) { return f; }
 
 // ---------------------------------------------------------------------------
 // Storage codecs.  The store keeps, for every direction i and node n, the pair
@@ -116,12 +126,12 @@ template <typename R> struct Moments {
     R Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;   // sum c c f (pre-collision)
 };
 
-// rho, rho u and the pressure tensor from f; rho E from g; T from E = Cv T + u^2/2.
-// f, g are the raw stored values; for the deviation stores (DEV) the moment sums of
-// the rest state are added (the rest state carries no momentum and no off-diagonal
-// stress, by symmetry).
+// Moments of f: rho, rho u and (FULL) the pressure tensor sum c c f.  f holds the raw
+// stored values; for the deviation stores (DEV) the moment sums of the rest state are
+// added (the rest state carries no momentum and no off-diagonal stress, by symmetry).
 template <int D, typename R, bool FULL, bool DEV>
-__device__ __forceinline__ void node_moments(const R* f, const R* g, const KParams& p, Moments<R>& m) {
+__device__ __forceinline__ void f_moments(const R* f, const KParams& p, R& rho, R& jx, R& jy, R& jz,
+                                          R P6[6]) {
     constexpr int NC = Lat<D>::NC;
     // per (b, c) row sums over c_x
     R t[3][3], d[3][3], e[3][3];
@@ -148,10 +158,12 @@ __device__ __forceinline__ void node_moments(const R* f, const R* g, const KPara
             eb[b] = (e[b][0] + e[b][2]) + e[b][1];
         }
     }
-    const R rho_ = (tb[0] + tb[2]) + tb[1];
-    R rho = rho_, jx = (db[0] + db[2]) + db[1], Pxx = (eb[0] + eb[2]) + eb[1];
-    R jy = tb[2] - tb[0], Pyy = tb[2] + tb[0], Pxy = db[2] - db[0];
-    R jz = 0, Pzz = 0, Pxz = 0, Pyz = 0;
+    rho = (tb[0] + tb[2]) + tb[1];
+    jx = (db[0] + db[2]) + db[1];
+    jy = tb[2] - tb[0];
+    jz = 0;
+    R Pxx = (eb[0] + eb[2]) + eb[1], Pyy = tb[2] + tb[0], Pxy = db[2] - db[0];
+    R Pzz = 0, Pxz = 0, Pyz = 0;
     if (D == 3) {
         const R tzh = (t[0][2] + t[2][2]) + t[1][2], tzl = (t[0][0] + t[2][0]) + t[1][0];
         const R dzh = (d[0][2] + d[2][2]) + d[1][2], dzl = (d[0][0] + d[2][0]) + d[1][0];
@@ -160,7 +172,21 @@ __device__ __forceinline__ void node_moments(const R* f, const R* g, const KPara
         Pxz = dzh - dzl;
         Pyz = (t[2][2] - t[0][2]) - (t[2][0] - t[0][0]);
     }
-    // sum of g as a balanced tree (short dependency chains)
+    if constexpr (DEV) {
+        rho += R(p.rest_rho);
+        Pxx += R(p.rest_Pxx);
+        Pyy += R(p.rest_Pyy);
+        Pzz += R(p.rest_Pzz);
+    }
+    if (FULL) {
+        P6[0] = Pxx; P6[1] = Pyy; P6[2] = Pzz;
+        P6[3] = Pxy; P6[4] = Pxz; P6[5] = Pyz;
+    }
+}
+
+// rho E = sum of g, as a balanced tree (short dependency chains).
+template <int D, typename R, bool DEV>
+__device__ __forceinline__ R g_energy(const R* g, const KParams& p) {
     R gs[Lat<D>::Q];
 #pragma unroll
     for (int i = 0; i < Lat<D>::Q; ++i) gs[i] = g[i];
@@ -169,13 +195,13 @@ __device__ __forceinline__ void node_moments(const R* f, const R* g, const KPara
 #pragma unroll
         for (int i = 0; i + w < Lat<D>::Q; i += 2 * w) gs[i] += gs[i + w];
     R rE = gs[0];
-    if constexpr (DEV) {
-        rho += R(p.rest_rho);
-        rE += R(p.rest_E);
-        Pxx += R(p.rest_Pxx);
-        Pyy += R(p.rest_Pyy);
-        Pzz += R(p.rest_Pzz);
-    }
+    if constexpr (DEV) rE += R(p.rest_E);
+    return rE;
+}
+
+// u = j / rho and T from E = Cv T + u^2/2.
+template <typename R>
+__device__ __forceinline__ void finish_moments(R rho, R jx, R jy, R jz, R rE, const KParams& p, Moments<R>& m) {
     const R inv = qdiv(R(1), rho);
     m.rho = rho;
     m.rE = rE;
@@ -183,10 +209,19 @@ __device__ __forceinline__ void node_moments(const R* f, const R* g, const KPara
     m.uy = jy * inv;
     m.uz = jz * inv;
     const R u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
-    m.T = (rE * inv - R(0.5) * u2) * R(p.gm1);
+    m.T = (rE * inv - R(0.5) * u2) * par<R>(p.gm1, p.f_gm1);
+}
+
+// All moments of one node: f_moments, g_energy, finish_moments.
+template <int D, typename R, bool FULL, bool DEV>
+__device__ __forceinline__ void node_moments(const R* f, const R* g, const KParams& p, Moments<R>& m) {
+    R rho, jx, jy, jz, P6[6];
+    f_moments<D, R, FULL, DEV>(f, p, rho, jx, jy, jz, P6);
+    const R rE = g_energy<D, R, DEV>(g, p);
+    finish_moments(rho, jx, jy, jz, rE, p, m);
     if (FULL) {
-        m.Pxx = Pxx; m.Pyy = Pyy; m.Pzz = Pzz;
-        m.Pxy = Pxy; m.Pxz = Pxz; m.Pyz = Pyz;
+        m.Pxx = P6[0]; m.Pyy = P6[1]; m.Pzz = P6[2];
+        m.Pxy = P6[3]; m.Pxz = P6[4]; m.Pyz = P6[5];
     }
 }
 
@@ -268,26 +303,28 @@ __device__ __forceinline__ void equilibria(R rho, R ux, R uy, R uz, R T, R Cv, R
     }
 }
 
-// One collision in place on the raw stored values f, g (populations, or their
-// deviations from the rest state when DEV).  D_a is the discrete derivative of
-// Q~_aaa at the node.  The BGK updates are written as
-//   f_i <- (1 - w) f_i + w f^ex_i,   g_i <- (1 - w1) g_i + w1 g^eq_i + corrections,
-// with w and w1 folded into the row factors of the product forms; for DEV the rest
-// state r_i is carried as (1 - w)(r_i + d_i) + w f^ex_i - r_i = (1 - w) d_i +
-// w (f^ex_i - r_i).
-template <int D, typename R, bool DEV>
-__device__ __forceinline__ void collide(R* f, R* g, const Moments<R>& m, R Dx, R Dy, R Dz,
-                                        const KParams& p) {
-    const R rho = m.rho, T = m.T, ux = m.ux, uy = m.uy, uz = m.uz;
-    // relaxation rates (Eqs. mu, Pr) from the local pressure P = rho T
-    R mu = R(p.mu0);
-    if (p.mu_exp != 0.0) mu = mu * qpow(T * R(1.0 / p.T0), R(p.mu_exp));
+// Relaxation rate omega (Eqs. mu, Pr) from the local pressure P = rho T, and omega_1.
+template <typename R>
+__device__ __forceinline__ R rate_w(R rho, R T, const KParams& p) {
+    R mu = par<R>(p.mu0, p.f_mu0);
+    if (p.powlaw) mu = mu * qpow(T * par<R>(p.d_invT0, p.f_invT0), par<R>(p.mu_exp, p.f_mu_exp));
     const R P = rho * T;
-    const R w = qdiv(R(2) * P, R(2) * mu + P);
-    const R Pr = R(p.Pr);
-    const R w1 = qdiv(R(2) * Pr * w, R(2) - w + Pr * w);
-    const R Cv = R(1.0 / p.gm1);
+    return qdiv(R(2) * P, R(2) * mu + P);
+}
+template <typename R>
+__device__ __forceinline__ R rate_w1(R w, const KParams& p) {
+    const R Pr = par<R>(p.Pr, p.f_Pr);
+    return qdiv(R(2) * Pr * w, R(2) - w + Pr * w);
+}
 
+// The f half of one collision, in place on the raw stored values f (populations, or
+// their deviations from the rest state when DEV).  D_a is the discrete derivative of
+// Q~_aaa at the node.  The BGK update is written as f_i <- (1 - w) f_i + w f^ex_i,
+// with w folded into the row factors of the product form; for DEV the rest state r_i
+// is carried as (1 - w)(r_i + d_i) + w f^ex_i - r_i = (1 - w) d_i + w (f^ex_i - r_i).
+template <int D, typename R, bool DEV>
+__device__ __forceinline__ void relax_f(R* f, const Moments<R>& m, R w, R Dx, R Dy, R Dz, const KParams& p) {
+    const R rho = m.rho, T = m.T, ux = m.ux, uy = m.uy, uz = m.uz;
     // extended f-equilibrium (Eqs. Pa_star, extf)
     const R k = qdiv(R(2) - w, R(2) * rho * w);
     R X[3], Y[3], Z[3];
@@ -311,8 +348,16 @@ __device__ __forceinline__ void collide(R* f, R* g, const Moments<R>& m, R Dx, R
             }
         }
     }
+}
 
-    // g-equilibrium (Eq. geq_i) relaxed with omega_1
+// The g half: g_i <- (1 - w1) g_i + w1 g^eq_i (Eq. geq_i, w1 folded in as above), then
+// the quasi-equilibrium correction (Eqs. gstar, qstar1).  m must carry the pressure
+// tensor (FULL moments).
+template <int D, typename R, bool DEV>
+__device__ __forceinline__ void relax_g(R* g, const Moments<R>& m, R w, R Dx, R Dy, R Dz, const KParams& p) {
+    const R rho = m.rho, T = m.T, ux = m.ux, uy = m.uy, uz = m.uz;
+    const R w1 = rate_w1(w, p);
+    const R Cv = par<R>(p.d_Cv, p.f_Cv);
     R gx[3], gy[3], gz[3], sx[3], sy[3], sz[3];
     gfactors(ux, T, gx, sx);
     gfactors(uy, T, gy, sy);
@@ -341,8 +386,8 @@ __device__ __forceinline__ void collide(R* f, R* g, const Moments<R>& m, R Dx, R
         }
     }
 
-    // quasi-equilibrium (Eqs. gstar, qstar1): q* - q^eq = u.(P - P^eq + div Q~ / 2),
-    // P^eq = rho T I + rho u u, div Q~ = diag(D); only |c_i| = 1 populations change,
+    // quasi-equilibrium: q* - q^eq = u.(P - P^eq + div Q~ / 2), P^eq = rho T I + rho u u,
+    // div Q~ = diag(D); only |c_i| = 1 populations change,
     // g_i += (omega - omega_1)(g^eq_i - g*_i) = -(omega - omega_1) c_i.(q* - q^eq) / 2.
     const R rT = rho * T;
     const R dxx = m.Pxx - rT - rho * ux * ux, dyy = m.Pyy - rT - rho * uy * uy;
@@ -368,6 +413,16 @@ __device__ __forceinline__ void collide(R* f, R* g, const Moments<R>& m, R Dx, R
         g[4] += h * dqz;         // (0,0,-1)
         g[22] -= h * dqz;        // (0,0,+1)
     }
+}
+
+// One collision in place on the raw stored values f, g: both halves above with the
+// same omega.
+template <int D, typename R, bool DEV>
+__device__ __forceinline__ void collide(R* f, R* g, const Moments<R>& m, R Dx, R Dy, R Dz,
+                                        const KParams& p) {
+    const R w = rate_w(m.rho, m.T, p);
+    relax_f<D, R, DEV>(f, m, w, Dx, Dy, Dz, p);
+    relax_g<D, R, DEV>(g, m, w, Dx, Dy, Dz, p);
 }
 
 }  // namespace elbm
