@@ -660,12 +660,12 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
         // EARLY: plane z is read into registers and plane z+2 requested before the
         // moments of plane z+1, so the copy overlaps them too (both planes are live
         // in registers meanwhile, which only a one-CTA-per-SM launch affords)
-        R f[Q], g[Q];
+        P pk[Q];   // the pulled pairs of plane z, as stored
         if (EARLY) {
             if (active) {
                 const P* bb = buf + (size_t)sz * Q * NS + tid;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], f[i], g[i]);
+                for (int i = 0; i < Q; ++i) pk[i] = bb[i * NS];
             }
             if (z + 2 <= ze) issue_plane(map_axis(z + 2, p.nz, p.per_z), sz, z + 2 < ze);
         }
@@ -689,7 +689,7 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
             if (active) {
                 const P* bb = buf + (size_t)sz * Q * NS + tid;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], f[i], g[i]);
+                for (int i = 0; i < Q; ++i) pk[i] = bb[i * NS];
             }
             if (z + 2 <= ze) issue_plane(map_axis(z + 2, p.nz, p.per_z), sz, z + 2 < ze);
         }
@@ -701,8 +701,16 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
             R v[5];
             node_totals(m_cur, m_cur.rE, v);
             acc.add(v);
-            collide<kD, R, DEV>(f, g, m_cur, Dx, Dy, Dz, p);
-            store_node(p, dst, node_index(p, x, y, z), f, g);
+            // collide and store pair by pair, decoding each just before its update
+            Relax<kD, R, DEV> rx;
+            rx.init(m_cur, Dx, Dy, Dz, p);
+            const unsigned n = (unsigned)node_index(p, x, y, z);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                R f, g;
+                Cd::dec(pk[i], f, g);
+                (dst + (size_t)i * (size_t)p.N)[n] = Cd::enc(rx.f(i, f, p), rx.g(i, g, p));
+            }
         }
         m_cur = m_next;
         qz_prev = qz_cur;
@@ -815,7 +823,8 @@ constexpr int kTotalsBlocks = 2 * 152;   // totals_kernel grid (grid-stride)
 // room and measured 35 % slower); FP16/BF16 pairs are half the size (two CTAs per
 // SM); FP64 uses the re-read kernel (its plane buffers would not fit).  With one CTA
 // per SM the registers also hold plane z while plane z+1's moments are computed, so
-// the prefetch of plane z+2 starts one phase earlier (EARLY; 10 % faster at 256^3).
+// the prefetch of plane z+2 starts one phase earlier (EARLY; 10 % faster at 256^3;
+// with two CTAs per SM and 128 registers it measured 1 % slower).
 #ifndef ELBM_PIPE_NB_F32
 #define ELBM_PIPE_NB_F32 2
 #endif

@@ -317,112 +317,107 @@ __device__ __forceinline__ R rate_w1(R w, const KParams& p) {
     return qdiv(R(2) * Pr * w, R(2) - w + Pr * w);
 }
 
-// The f half of one collision, in place on the raw stored values f (populations, or
-// their deviations from the rest state when DEV).  D_a is the discrete derivative of
-// Q~_aaa at the node.  The BGK update is written as f_i <- (1 - w) f_i + w f^ex_i,
-// with w folded into the row factors of the product form; for DEV the rest state r_i
-// is carried as (1 - w)(r_i + d_i) + w f^ex_i - r_i = (1 - w) d_i + w (f^ex_i - r_i).
+// One collision, direction by direction.  init() evaluates the per-node factors;
+// f(i, f_i) and g(i, g_i) return the post-collision values of direction i from the raw
+// stored values (populations, or their deviations from the rest state when DEV).
+//   f_i <- (1 - w) f_i + w f^ex_i            (Eqs. fLBGK, extf, Pa_star)
+//   g_i <- (1 - w1) g_i + w1 g^eq_i + corr_i (Eqs. gLBGK, geq_i, gstar, qstar1)
+// with w and w1 folded into the row factors of the product forms.  For DEV the rest
+// state r_i is carried as (1 - w)(r_i + d_i) + w f^ex_i - r_i = (1 - w) d_i +
+// w (f^ex_i - r_i).  corr_i is the quasi-equilibrium term, nonzero only for |c_i| = 1:
+// q* - q^eq = u.(P - P^eq + div Q~ / 2) with P^eq = rho T I + rho u u and
+// div Q~ = diag(D), and g_i += (omega - omega_1)(g^eq_i - g*_i) =
+// -(omega - omega_1) c_i.(q* - q^eq) / 2.  m must carry the pressure tensor.
 template <int D, typename R, bool DEV>
-__device__ __forceinline__ void relax_f(R* f, const Moments<R>& m, R w, R Dx, R Dy, R Dz, const KParams& p) {
-    const R rho = m.rho, T = m.T, ux = m.ux, uy = m.uy, uz = m.uz;
-    // extended f-equilibrium (Eqs. Pa_star, extf)
-    const R k = qdiv(R(2) - w, R(2) * rho * w);
-    R X[3], Y[3], Z[3];
-    psi3(ux, T + ux * ux + k * Dx, X);
-    psi3(uy, T + uy * uy + k * Dy, Y);
-    if (D == 3) psi3(uz, T + uz * uz + k * Dz, Z);
-    else { Z[0] = Z[2] = 0; Z[1] = 1; }
-    const R omw = R(1) - w, wr = w * rho;
+struct Relax {
+    R omw, omw1, w, w1;
+    R X[3], Y[3], Z[3], wr;                      // f^ex factors
+    R gx[3], gy[3], gz[3], sy[3], sz[3], ax[3];  // g^eq factors
+    R w1r;
+    R h, dq[3];                                  // (omega - omega_1)/2 and q* - q^eq
+
+    __device__ __forceinline__ void init(const Moments<R>& m, R Dx, R Dy, R Dz, const KParams& p) {
+        const R rho = m.rho, T = m.T, ux = m.ux, uy = m.uy, uz = m.uz;
+        w = rate_w(rho, T, p);
+        w1 = rate_w1(w, p);
+        // extended f-equilibrium
+        const R k = qdiv(R(2) - w, R(2) * rho * w);
+        psi3(ux, T + ux * ux + k * Dx, X);
+        psi3(uy, T + uy * uy + k * Dy, Y);
+        if (D == 3) psi3(uz, T + uz * uz + k * Dz, Z);
+        else { Z[0] = Z[2] = 0; Z[1] = 1; }
+        omw = R(1) - w;
+        wr = w * rho;
+        // g-equilibrium
+        const R Cv = par<R>(p.d_Cv, p.f_Cv);
+        R sx[3];
+        gfactors(ux, T, gx, sx);
+        gfactors(uy, T, gy, sy);
+        if (D == 3) gfactors(uz, T, gz, sz);
+        else { gz[0] = gz[2] = 0; gz[1] = 1; sz[0] = sz[1] = sz[2] = 0; }
+        const R CvT = Cv * T;
 #pragma unroll
-    for (int c = 0; c < Lat<D>::NC; ++c) {
-        const int cc = (D == 3) ? c : 1;
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const R yz = wr * Y[b] * Z[cc];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const int i = a + 3 * b + 9 * c;
-                R t = X[a] * yz;
-                if constexpr (DEV) t = fma(-w, R(p.rest32[i]), t);
-                f[i] = fma(omw, f[i], t);
-            }
+        for (int a = 0; a < 3; ++a) ax[a] = CvT * gx[a] + sx[a];
+        omw1 = R(1) - w1;
+        w1r = w1 * rho;
+        // quasi-equilibrium
+        const R rT = rho * T;
+        const R dxx = m.Pxx - rT - rho * ux * ux, dyy = m.Pyy - rT - rho * uy * uy;
+        const R dxy = m.Pxy - rho * ux * uy;
+        R dqx = ux * dxx + uy * dxy + R(0.5) * ux * Dx;
+        R dqy = ux * dxy + uy * dyy + R(0.5) * uy * Dy;
+        R dqz = 0;
+        if (D == 3) {
+            const R dzz = m.Pzz - rT - rho * uz * uz;
+            const R dxz = m.Pxz - rho * ux * uz, dyz = m.Pyz - rho * uy * uz;
+            dqx += uz * dxz;
+            dqy += uz * dyz;
+            dqz = ux * dxz + uy * dyz + uz * dzz + R(0.5) * uz * Dz;
         }
+        h = R(0.5) * (w - w1);
+        dq[0] = dqx;
+        dq[1] = dqy;
+        dq[2] = dqz;
     }
-}
 
-// The g half: g_i <- (1 - w1) g_i + w1 g^eq_i (Eq. geq_i, w1 folded in as above), then
-// the quasi-equilibrium correction (Eqs. gstar, qstar1).  m must carry the pressure
-// tensor (FULL moments).
-template <int D, typename R, bool DEV>
-__device__ __forceinline__ void relax_g(R* g, const Moments<R>& m, R w, R Dx, R Dy, R Dz, const KParams& p) {
-    const R rho = m.rho, T = m.T, ux = m.ux, uy = m.uy, uz = m.uz;
-    const R w1 = rate_w1(w, p);
-    const R Cv = par<R>(p.d_Cv, p.f_Cv);
-    R gx[3], gy[3], gz[3], sx[3], sy[3], sz[3];
-    gfactors(ux, T, gx, sx);
-    gfactors(uy, T, gy, sy);
-    if (D == 3) gfactors(uz, T, gz, sz);
-    else { gz[0] = gz[2] = 0; gz[1] = 1; sz[0] = sz[1] = sz[2] = 0; }
-    const R CvT = Cv * T;
-    R ax[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) ax[a] = CvT * gx[a] + sx[a];
-    const R omw1 = R(1) - w1, w1r = w1 * rho;
-    constexpr int Q = Lat<D>::Q;
-#pragma unroll
-    for (int c = 0; c < Lat<D>::NC; ++c) {
-        const int cc = (D == 3) ? c : 1;
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const R A = w1r * gy[b] * gz[cc];
-            const R B = w1r * (sy[b] * gz[cc] + gy[b] * sz[cc]);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const int i = a + 3 * b + 9 * c;
-                R t = fma(ax[a], A, gx[a] * B);
-                if constexpr (DEV) t = fma(-w1, R(p.rest32[Q + i]), t);
-                g[i] = fma(omw1, g[i], t);
-            }
+    // i is a compile-time constant after unrolling, so every branch below folds away
+    __device__ __forceinline__ R f(int i, R fi, const KParams& p) const {
+        const int a = cx_of(i) + 1, b = cy_of(i) + 1, c = (D == 3) ? cz_of<D>(i) + 1 : 1;
+        const R yz = wr * Y[b] * Z[c];
+        R t = X[a] * yz;
+        if constexpr (DEV) t = fma(-w, R(p.rest32[i]), t);
+        return fma(omw, fi, t);
+    }
+    __device__ __forceinline__ R g(int i, R gi, const KParams& p) const {
+        constexpr int Q = Lat<D>::Q;
+        const int a = cx_of(i) + 1, b = cy_of(i) + 1, c = (D == 3) ? cz_of<D>(i) + 1 : 1;
+        const R A = w1r * gy[b] * gz[c];
+        const R B = w1r * (sy[b] * gz[c] + gy[b] * sz[c]);
+        R t = fma(ax[a], A, gx[a] * B);
+        if constexpr (DEV) t = fma(-w1, R(p.rest32[Q + i]), t);
+        R v = fma(omw1, gi, t);
+        // unit-speed directions: the correction enters with the sign of -c_i
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of<D>(i);
+        if (cx * cx + cy * cy + cz * cz == 1) {
+            const R q = cx != 0 ? dq[0] : (cy != 0 ? dq[1] : dq[2]);
+            if (cx + cy + cz < 0) v += h * q;
+            else v -= h * q;
         }
+        return v;
     }
+};
 
-    // quasi-equilibrium: q* - q^eq = u.(P - P^eq + div Q~ / 2), P^eq = rho T I + rho u u,
-    // div Q~ = diag(D); only |c_i| = 1 populations change,
-    // g_i += (omega - omega_1)(g^eq_i - g*_i) = -(omega - omega_1) c_i.(q* - q^eq) / 2.
-    const R rT = rho * T;
-    const R dxx = m.Pxx - rT - rho * ux * ux, dyy = m.Pyy - rT - rho * uy * uy;
-    const R dxy = m.Pxy - rho * ux * uy;
-    R dqx = ux * dxx + uy * dxy + R(0.5) * ux * Dx;
-    R dqy = ux * dxy + uy * dyy + R(0.5) * uy * Dy;
-    R dqz = 0;
-    if (D == 3) {
-        const R dzz = m.Pzz - rT - rho * uz * uz;
-        const R dxz = m.Pxz - rho * ux * uz, dyz = m.Pyz - rho * uy * uz;
-        dqx += uz * dxz;
-        dqy += uz * dyz;
-        dqz = ux * dxz + uy * dyz + uz * dzz + R(0.5) * uz * Dz;
-    }
-    const R h = R(0.5) * (w - w1);
-    // unit-speed directions: (-1,0,0)=a0, (+1,0,0)=a2 on row b=1, c=centre
-    constexpr int C0 = (D == 3) ? 9 : 0;
-    g[C0 + 3 + 0] += h * dqx;
-    g[C0 + 3 + 2] -= h * dqx;
-    g[C0 + 1] += h * dqy;        // (0,-1,0)
-    g[C0 + 7] -= h * dqy;        // (0,+1,0)
-    if (D == 3) {
-        g[4] += h * dqz;         // (0,0,-1)
-        g[22] -= h * dqz;        // (0,0,+1)
-    }
-}
-
-// One collision in place on the raw stored values f, g: both halves above with the
-// same omega.
+// One collision in place on the raw stored values f, g.
 template <int D, typename R, bool DEV>
 __device__ __forceinline__ void collide(R* f, R* g, const Moments<R>& m, R Dx, R Dy, R Dz,
                                         const KParams& p) {
-    const R w = rate_w(m.rho, m.T, p);
-    relax_f<D, R, DEV>(f, m, w, Dx, Dy, Dz, p);
-    relax_g<D, R, DEV>(g, m, w, Dx, Dy, Dz, p);
+    Relax<D, R, DEV> r;
+    r.init(m, Dx, Dy, Dz, p);
+#pragma unroll
+    for (int i = 0; i < Lat<D>::Q; ++i) {
+        f[i] = r.f(i, f[i], p);
+        g[i] = r.g(i, g[i], p);
+    }
 }
 
 }  // namespace elbm
