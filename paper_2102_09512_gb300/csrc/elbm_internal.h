@@ -71,15 +71,15 @@ inline int fill_kparams(const elbm_params& p, KParams& k, int* D_out) {
         for (int i = 0; i < Q; ++i) {
             const int a = i % 3, b = (i / 3) % 3, c = D == 3 ? i / 9 : 1;
             const double pz = D == 3 ? phi[c] : 1.0, sz = D == 3 ? psi[c] : 0.0;
-            k.rest32[i] = (float)(p.rho_ref * phi[a] * phi[b] * pz);
-            k.rest32[Q + i] = (float)(p.rho_ref * ((Cv * T0 * phi[a] + psi[a]) * phi[b] * pz +
-                                                   phi[a] * (psi[b] * pz + phi[b] * sz)));
+            k.rest2[i].x = (float)(p.rho_ref * phi[a] * phi[b] * pz);
+            k.rest2[i].y = (float)(p.rho_ref * ((Cv * T0 * phi[a] + psi[a]) * phi[b] * pz +
+                                                phi[a] * (psi[b] * pz + phi[b] * sz)));
             // moment sums of the stored (rounded) rest values
-            srho += k.rest32[i];
-            if (a != 1) sxx += k.rest32[i];
-            if (b != 1) syy += k.rest32[i];
-            if (D == 3 && c != 1) szz += k.rest32[i];
-            sE += k.rest32[Q + i];
+            srho += k.rest2[i].x;
+            if (a != 1) sxx += k.rest2[i].x;
+            if (b != 1) syy += k.rest2[i].x;
+            if (D == 3 && c != 1) szz += k.rest2[i].x;
+            sE += k.rest2[i].y;
         }
         k.rest_rho = (float)srho;
         k.rest_Pxx = (float)sxx;

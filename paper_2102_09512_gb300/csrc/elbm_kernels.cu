@@ -202,8 +202,8 @@ __global__ void init_kernel(const __grid_constant__ KParams p, const double* __r
         if constexpr (DEV) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                f[i] -= R(p.rest32[i]);
-                g[i] -= R(p.rest32[Q + i]);
+                f[i] -= R(p.rest2[i].x);
+                g[i] -= R(p.rest2[i].y);
             }
         }
         store_node(p, pop, n, f, g);
@@ -564,17 +564,30 @@ struct Pipe {
     static constexpr size_t smem_bytes = buf_bytes + q_bytes;
 };
 
+// Base of every direction plane of the source and destination stores, computed on the
+// host: the kernel then forms each population address as one 32-bit node offset added
+// to a base read from the parameter bank, instead of a 64-bit i * N product per access.
+struct DirPlanes {
+    const P* src[Q];
+    P* dst[Q];
+};
+__device__ __forceinline__ const P* dir_src(const DirPlanes& pl, const PullRows& r, int i) {
+    const int a = i % 3, b = (i / 3) % 3, c = (kD == 3) ? i / 9 : 1;
+    return pl.src[i] + (unsigned)(r.row[b][c] + r.xs[a]);
+}
+
 template <int TY, int NB>
 struct PipeBytes {
     static constexpr size_t value = Pipe<TY, NB>::smem_bytes;
 };
 
-template <int TY, int NB, int MINB, bool EARLY>
+template <int TY, int NB, int MINB, bool EARLY, int DD>
 __global__ void __launch_bounds__(TX * TY, MINB)
-fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* __restrict__ dst,
-               double* __restrict__ partials, int* __restrict__ status) {
+fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPlanes pl,
+               const P* __restrict__ src, double* __restrict__ partials, int* __restrict__ status) {
     using PP = Pipe<TY, NB>;
     static_assert(NB == 2, "plane z+2 is prefetched into the slots of plane z");
+    static_assert(sizeof(R) == 4 && DD == 3, "the pipelined kernel is D3Q27 in FP32");
     constexpr int NT = PP::NT, NH = PP::NH, NS = PP::NS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     P* buf = reinterpret_cast<P*>(smem_raw);                       // [NB][Q][NS]
@@ -601,13 +614,13 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
             PullRows r;
             pull_rows(p, x, y, q, r);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) cp_async<sizeof(P)>(bb + i * NS + tid, src_ptr(p, src, r, i));
+            for (int i = 0; i < Q; ++i) cp_async<sizeof(P)>(bb + i * NS + tid, dir_src(pl, r, i));
         }
         if (with_halo && has_halo) {
             PullRows r;
             pull_rows(p, hx, hy, q, r);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) cp_async<sizeof(P)>(bb + i * NS + NT + tid, src_ptr(p, src, r, i));
+            for (int i = 0; i < Q; ++i) cp_async<sizeof(P)>(bb + i * NS + NT + tid, dir_src(pl, r, i));
         }
         cp_async_commit();
     };
@@ -709,7 +722,7 @@ fused3d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
             for (int i = 0; i < Q; ++i) {
                 R f, g;
                 Cd::dec(pk[i], f, g);
-                (dst + (size_t)i * (size_t)p.N)[n] = Cd::enc(rx.f(i, f, p), rx.g(i, g, p));
+                pl.dst[i][n] = Cd::enc(rx.f(i, f, p), rx.g(i, g, p));
             }
         }
         m_cur = m_next;
@@ -901,14 +914,18 @@ cudaError_t launch_fused(const KParams& p, const void* src, void* dst, double* p
         bool launched = false;
         if constexpr (kPipe) {
             if (!reread) {
-                auto kern = fused3d_kernel<kTY3, kNB, kMinB, kEarly>;
+                auto kern = fused3d_kernel<kTY3, kNB, kMinB, kEarly, DD>;
                 // the dynamic shared-memory limit is a per-function attribute; setting it
                 // again is cheap and keeps this correct for every device of the process
                 cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                      (int)PipeCfg::smem_bytes);
                 if (e != cudaSuccess) return e;
-                kern<<<grid, dim3(TX, kTY3), PipeCfg::smem_bytes, s>>>(p, (const P*)src, (P*)dst, partials,
-                                                                       status);
+                DirPlanes pl;
+                for (int i = 0; i < Q; ++i) {
+                    pl.src[i] = (const P*)src + (size_t)i * (size_t)p.N;
+                    pl.dst[i] = (P*)dst + (size_t)i * (size_t)p.N;
+                }
+                kern<<<grid, dim3(TX, kTY3), PipeCfg::smem_bytes, s>>>(p, pl, (const P*)src, partials, status);
                 launched = true;
             }
         }

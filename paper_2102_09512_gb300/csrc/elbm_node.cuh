@@ -31,7 +31,7 @@ struct KParams {
     double Pr, mu0, T0, mu_exp;
     int deriv;                   // 0 upwind, 1 central
     int tz;                      // z-segment length of the fused 3D kernels
-    float rest32[54];            // rest-state populations (f then g) of the deviation stores
+    float2 rest2[27];            // rest-state pair (f_i, g_i) of every direction, deviation stores
     float rest_rho, rest_Pxx, rest_Pyy, rest_Pzz, rest_E;   // their moment sums
     // The same parameters precomputed in both arithmetic types, so that no kernel
     // converts or divides a double per node (the FP64 pipe of GB300 is narrow).
@@ -385,7 +385,7 @@ struct Relax {
         const int a = cx_of(i) + 1, b = cy_of(i) + 1, c = (D == 3) ? cz_of<D>(i) + 1 : 1;
         const R yz = wr * Y[b] * Z[c];
         R t = X[a] * yz;
-        if constexpr (DEV) t = fma(-w, R(p.rest32[i]), t);
+        if constexpr (DEV) t = fma(-w, R(p.rest2[i].x), t);
         return fma(omw, fi, t);
     }
     __device__ __forceinline__ R g(int i, R gi, const KParams& p) const {
@@ -394,7 +394,7 @@ struct Relax {
         const R A = w1r * gy[b] * gz[c];
         const R B = w1r * (sy[b] * gz[c] + gy[b] * sz[c]);
         R t = fma(ax[a], A, gx[a] * B);
-        if constexpr (DEV) t = fma(-w1, R(p.rest32[Q + i]), t);
+        if constexpr (DEV) t = fma(-w1, R(p.rest2[i].y), t);
         R v = fma(omw1, gi, t);
         // unit-speed directions: the correction enters with the sign of -c_i
         const int cx = cx_of(i), cy = cy_of(i), cz = cz_of<D>(i);
