@@ -144,6 +144,15 @@ int elbm_create(const elbm_params* prm, elbm_handle** out) {
     h->kernel = ELBM_KERNEL_FUSED;
 
     h->kp = kp;
+    if (D == 3) {
+        // z segments sized for the waves of this device (current device at creation)
+        int dev = -1, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            h->kp.tz = choose_tz(kp, h->ops->fused_tile_y, sms, h->ops->fused_occupancy(), kp.tz);
+        else
+            cudaGetLastError();   // no device: keep the fallback, clear the error
+    }
     const KParams& k = h->kp;
 
     h->pop_bytes = (size_t)2 * h->Q * (size_t)N * h->ops->value_bytes;

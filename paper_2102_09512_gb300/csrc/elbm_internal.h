@@ -139,7 +139,37 @@ struct Ops {
     int (*ensemble_occupancy)(int ty);
     cudaError_t (*stats)(const KParams& p, const void* pop, double* partials, int* nblocks, cudaStream_t s,
                          long long* launches);   // 8 partial sums per CTA
+    int fused_tile_y;             // tile height of the fused kernels (tile width 32)
+    int (*fused_occupancy)();     // resident CTAs per SM of the default fused D3Q27 kernel (0: unknown)
 };
+
+// z-segment length of the fused D3Q27 kernels.  Each CTA marches one (tile, segment)
+// column; the grid runs in waves of sms * per_sm CTAs.  The choice maximises the fill
+// of the last wave times tz / (tz + 2), the second factor charging each segment about
+// two planes of prologue (the Q~ plane below it and the plane above it).  Ties keep
+// the longer segment.  Without device information the fallback is kept.
+inline int choose_tz(const KParams& k, int ty, int sms, int per_sm, int fallback) {
+    if (sms <= 0 || per_sm <= 0) return fallback < k.nz ? fallback : k.nz;
+    const double tiles = (double)((k.nx + 31) / 32) * (double)((k.ny + ty - 1) / ty);
+    const double slots = (double)sms * per_sm;
+    const int lo = k.nz < 16 ? k.nz : 16, hi = 128;
+    int best = fallback < k.nz ? fallback : k.nz;
+    double best_score = -1.0;
+    for (int nseg = 1; nseg <= k.nz; ++nseg) {
+        const int tz = (k.nz + nseg - 1) / nseg;
+        if (tz > hi) continue;
+        if (tz < lo) break;
+        const int ns = (k.nz + tz - 1) / tz;
+        const double waves = tiles * ns / slots;
+        const double fill = waves / std::ceil(waves);
+        const double score = fill * tz / (tz + 2.0);
+        if (score > best_score + 1e-9) {
+            best_score = score;
+            best = tz;
+        }
+    }
+    return best;
+}
 
 const Ops* ops_d2_f64();
 const Ops* ops_d2_f32();

@@ -991,9 +991,30 @@ cudaError_t launch_totals(const KParams& p, const void* pop, double* partials, i
     return cudaGetLastError();
 }
 
+// Resident CTAs per SM of the default fused D3Q27 kernel (a template so that the
+// kernel of the other lattice is never instantiated).
+template <int DD>
+int fused_occupancy_impl() {
+    int n = 0;
+    if constexpr (DD == 3 && kPipe) {
+        auto kern = fused3d_kernel<kTY3, kNB, kMinB, kEarly, DD>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PipeCfg::smem_bytes) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX * kTY3, PipeCfg::smem_bytes) != cudaSuccess)
+            return 0;
+    } else if constexpr (DD == 3) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused3d_reread_kernel<kTY3>, TX * kTY3, 0) !=
+            cudaSuccess)
+            return 0;
+    }
+    return n;
+}
+int fused_occupancy() { return fused_occupancy_impl<kD>(); }
+
 const Ops kOps = {kD,          kST,           sizeof(P) / 2,  sizeof(R),            max_blocks,
                   launch_init, launch_fields, launch_twopass, launch_fused_default, launch_fused_reread,
-                  launch_totals, launch_ensemble, ensemble_occupancy, launch_stats};
+                  launch_totals, launch_ensemble, ensemble_occupancy, launch_stats,
+                  kD == 3 ? kTY3 : kTY2, fused_occupancy};
 
 }  // namespace
 
