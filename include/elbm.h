@@ -135,9 +135,11 @@ int elbm_step_totals(elbm_handle *h, double out[5]);
 
 /* Turbulence statistics of the current state (paper Sec. III.D), volume averages
  * over all nodes, FP64: out = {<rho>, rho_rms, K = <rho u.u>/2, u_rms = sqrt(<u.u>/D),
- * theta_rms = sqrt(<(div u)^2>), <T>, T_rms, <(d u_x/d x)^2>}; derivatives by
- * second-order central differences (ghosts from the boundary map).  Synchronises. */
-int elbm_turbulence_stats(elbm_handle *h, double out[8]);
+ * theta_rms = sqrt(<(div u)^2>), <T>, T_rms, <(d u_x/d x)^2>,
+ * omega_rms = sqrt(<|omega|^2>), enstrophy = <|omega|^2>/2} with omega = curl u;
+ * derivatives by second-order central differences (ghosts from the boundary map).
+ * out holds 10 doubles (caller-owned).  Synchronises. */
+int elbm_turbulence_stats(elbm_handle *h, double out[10]);
 
 /* Selects the kernel schedule (elbm_kernel).  Results agree to rounding. */
 int elbm_set_kernel(elbm_handle *h, int kernel);

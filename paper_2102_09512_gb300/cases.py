@@ -14,6 +14,7 @@ Set-ups (paper Sec. III):
   - :func:`hit`           solenoidal random field with E(k) ~ k^4 exp(-2 (k/k0)^2)
                           (Sec. III.D), with mu0 from Re_lambda
   - :func:`ensemble`      uneven 2D instances (Sod / shock-vortex mix)
+  - :func:`isentropic_vortex`  vortex carried by a uniform flow (translation pin)
   - :func:`shear_wave`, :func:`sound_wave`, :func:`thermal_wave`, :func:`random_smooth`
                           small-amplitude and random fields for tests
 """
@@ -237,6 +238,28 @@ def thermal_wave(D: int = 2, L: int = 64, A: float = 1e-4, rho0: float = 1.0, T0
     T[:] = T0 * (1.0 + A * np.cos(2.0 * math.pi * x / L))
     rho[:] = rho0 * T0 / T
     return Case("thermal_wave", D, L, n_other, nz, rho, u, T, gamma=gamma, Pr=Pr, mu0=mu, T0=T0)
+
+
+def isentropic_vortex(L: int = 48, U0: float = 0.2, Ma_v: float = 0.2, r_v: float = 6.0,
+                      rho0: float = 1.0, T0: float = 0.15, mu: float = 1e-3, Pr: float = 0.71,
+                      gamma: float = 1.4) -> Case:
+    """Isentropic vortex of Mach Ma_v and radius r_v (the vortex of Sec. III.C) at the
+    centre of a periodic L x L box, carried by a uniform flow u_x = U0.  The Euler
+    solution translates it unchanged: after t steps its centre is at
+    (L/2 + U0 t, L/2) modulo L."""
+    rho, u, T = _empty(2, L, L, 1)
+    x, y, _ = _grid(2, L, L, 1)
+    xv = yv = L / 2.0
+    cs = math.sqrt(gamma * T0)
+    r2 = ((x - xv) ** 2 + (y - yv) ** 2) / (r_v * r_v)
+    base = 1.0 - 0.5 * (gamma - 1.0) * Ma_v * Ma_v * np.exp(1.0 - r2)
+    rho[:] = rho0 * base ** (1.0 / (gamma - 1.0))
+    T[:] = T0 * base
+    amp = cs * Ma_v * np.exp(0.5 * (1.0 - r2))
+    u[0] = U0 + amp * (y - yv) / r_v
+    u[1] = -amp * (x - xv) / r_v
+    return Case("isentropic_vortex", 2, L, L, 1, rho, u, T, gamma=gamma, Pr=Pr, mu0=mu, T0=T0,
+                extra=dict(U0=U0, x_v=xv, y_v=yv, r_v=r_v))
 
 
 def random_smooth(D: int, nx: int, ny: int, nz: int = 1, seed: int = 0, rho0: float = 1.0,

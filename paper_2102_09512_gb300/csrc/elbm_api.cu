@@ -56,9 +56,12 @@ const Ops* pick_ops(int D, int store) {
     return nullptr;
 }
 
-// Compensated FP64 sum over nb partial vectors of `width` values (width <= 8).
+// Compensated FP64 sum over nb partial vectors of `width` values (width <= kMaxWidth).
+constexpr int kMaxWidth = 10;   // widest partial vector: step totals 5, statistics kStatsSums
+static_assert(kStatsSums <= kMaxWidth, "finalize width");
+
 __global__ void finalize_kernel(const double* __restrict__ partials, int nb, int width, double* __restrict__ out) {
-    double s[8] = {0, 0, 0, 0, 0, 0, 0, 0}, c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double s[kMaxWidth] = {}, c[kMaxWidth] = {};
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
         for (int k = 0; k < width; ++k) {   // Neumaier
             const double v = partials[(size_t)width * j + k];
@@ -67,7 +70,7 @@ __global__ void finalize_kernel(const double* __restrict__ partials, int nb, int
             s[k] = t;
         }
     }
-    __shared__ double red[8][256];
+    __shared__ double red[kMaxWidth][256];
     for (int k = 0; k < width; ++k) red[k][threadIdx.x] = s[k] + c[k];
     __syncthreads();
     if (threadIdx.x < width) {   // fixed-order compensated sum of the 256 thread values
@@ -88,7 +91,7 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? ELBM_OK : ELBM_ERR_CU
 int* status_ptr(elbm_handle* h) { return (int*)(h->auxp + h->aux.status); }
 double* totals_ptr(elbm_handle* h) { return (double*)(h->auxp + h->aux.totals); }
 double* step_partials(elbm_handle* h) { return (double*)(h->auxp + h->aux.partials); }
-// query partials hold up to 8 values per CTA (turbulence statistics)
+// query partials hold up to kStatsSums values per CTA (turbulence statistics)
 double* query_partials(elbm_handle* h) {
     return (double*)(h->auxp + h->aux.partials) + 5 * (size_t)h->aux.max_blocks;
 }
@@ -162,9 +165,9 @@ int elbm_create(const elbm_params* prm, elbm_handle** out) {
     a.status = off;
     off = align_up(off + sizeof(int));
     a.totals = off;
-    off = align_up(off + 8 * sizeof(double));
+    off = align_up(off + kMaxWidth * sizeof(double));
     a.partials = off;
-    off = align_up(off + (5 + 8) * sizeof(double) * (size_t)a.max_blocks);
+    off = align_up(off + (5 + kStatsSums) * sizeof(double) * (size_t)a.max_blocks);
     a.qfield = off;
     off = align_up(off + (size_t)D * N * h->ops->real_bytes);
     a.staging = off;
@@ -266,14 +269,14 @@ int elbm_conservation(elbm_handle* h, double out[5]) {
     return finalize_to_host(h, query_partials(h), nb, out);
 }
 
-int elbm_turbulence_stats(elbm_handle* h, double out[8]) {
+int elbm_turbulence_stats(elbm_handle* h, double out[10]) {
     if (!h || !h->bound || !out) return ELBM_ERR_ARG;
     int nb = 0;
-    double* part = query_partials(h);   // 8 values x (<= max_blocks) CTAs
+    double* part = query_partials(h);   // kStatsSums values x (<= max_blocks) CTAs
     cudaError_t e = h->ops->stats(h->kp, h->pop[h->cur], part, &nb, h->stream, &h->launches);
     if (e != cudaSuccess) return ELBM_ERR_CUDA;
-    double sums[8];
-    const int rc = finalize_to_host(h, part, nb, sums, 8);
+    double sums[kStatsSums];
+    const int rc = finalize_to_host(h, part, nb, sums, kStatsSums);
     if (rc != ELBM_OK) return rc;
     const double N = (double)h->N;
     const double mrho = sums[0] / N, mT = sums[5] / N;
@@ -285,6 +288,8 @@ int elbm_turbulence_stats(elbm_handle* h, double out[8]) {
     out[5] = mT;                                                 // <T>
     out[6] = std::sqrt(std::fmax(sums[6] / N - mT * mT, 0.0));   // T_rms
     out[7] = sums[7] / N;                                        // <(d u_x/d x)^2>
+    out[8] = std::sqrt(sums[8] / N);                             // omega_rms = sqrt(<|omega|^2>)
+    out[9] = 0.5 * sums[8] / N;                                  // enstrophy = <|omega|^2>/2
     return ELBM_OK;
 }
 

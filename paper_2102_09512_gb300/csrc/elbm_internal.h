@@ -115,6 +115,9 @@ struct EnsembleArgs {
 
 // Launchers for one (lattice, store) combination.  Each returns the first CUDA
 // error it meets and adds the number of kernels it launched to *launches.
+// Per-CTA partial sums of the turbulence statistics (stats_kernel, elbm_turbulence_stats).
+constexpr int kStatsSums = 9;
+
 struct Ops {
     int D, store;
     size_t value_bytes;   // bytes per stored population value
@@ -138,7 +141,7 @@ struct Ops {
                                  int grid, cudaStream_t s, long long* launches);
     int (*ensemble_occupancy)(int ty);
     cudaError_t (*stats)(const KParams& p, const void* pop, double* partials, int* nblocks, cudaStream_t s,
-                         long long* launches);   // 8 partial sums per CTA
+                         long long* launches);   // kStatsSums partial sums per CTA
     int fused_tile_y;             // tile height of the fused kernels (tile width 32)
     int (*fused_occupancy)();     // resident CTAs per SM of the default fused D3Q27 kernel (0: unknown)
 };

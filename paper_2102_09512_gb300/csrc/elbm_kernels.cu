@@ -285,13 +285,14 @@ __device__ __forceinline__ void node_velocity(const KParams& p, const P* __restr
 }
 
 // Turbulence statistics of the current state (one FP64 partial vector per CTA):
-// sums of rho, rho^2, rho u.u, u.u, theta^2, T, T^2 and (d u_x / d x)^2 with the
-// dilatation theta = div u and d u_x / d x by second-order central differences
-// (boundary nodes use the ghost values of the boundary map).
-constexpr int kStats = 8;
+// sums of rho, rho^2, rho u.u, u.u, theta^2, T, T^2, (d u_x / d x)^2 and |omega|^2,
+// with the velocity gradient by second-order central differences (boundary nodes use
+// the ghost values of the boundary map): dilatation theta = div u, vorticity
+// omega = curl u.
+constexpr int kStats = kStatsSums;
 __global__ void stats_kernel(const __grid_constant__ KParams p, const P* __restrict__ pop,
                              double* __restrict__ partials) {
-    double acc[kStats] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double acc[kStats] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < p.N;
          n += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((long long)p.nx * p.ny));
@@ -299,19 +300,24 @@ __global__ void stats_kernel(const __grid_constant__ KParams p, const P* __restr
         load_local(p, pop, n, f, g);
         Moments<R> m;
         node_moments<kD, R, false, DEV>(f, g, p, m);
+        double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // G[a][b] = d u_a / d x_b
         R up[3], um[3];
         node_velocity(p, pop, node_index(p, map_axis(x + 1, p.nx, p.per_x), y, z), up);
         node_velocity(p, pop, node_index(p, map_axis(x - 1, p.nx, p.per_x), y, z), um);
-        const double dux = 0.5 * ((double)up[0] - (double)um[0]);
-        double theta = dux;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) G[a][0] = 0.5 * ((double)up[a] - (double)um[a]);
         node_velocity(p, pop, node_index(p, x, map_axis(y + 1, p.ny, p.per_y), z), up);
         node_velocity(p, pop, node_index(p, x, map_axis(y - 1, p.ny, p.per_y), z), um);
-        theta += 0.5 * ((double)up[1] - (double)um[1]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) G[a][1] = 0.5 * ((double)up[a] - (double)um[a]);
         if (kD == 3) {
             node_velocity(p, pop, node_index(p, x, y, map_axis(z + 1, p.nz, p.per_z)), up);
             node_velocity(p, pop, node_index(p, x, y, map_axis(z - 1, p.nz, p.per_z)), um);
-            theta += 0.5 * ((double)up[2] - (double)um[2]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) G[a][2] = 0.5 * ((double)up[a] - (double)um[a]);
         }
+        const double theta = G[0][0] + G[1][1] + G[2][2];
+        const double wx = G[2][1] - G[1][2], wy = G[0][2] - G[2][0], wz = G[1][0] - G[0][1];
         const double rho = m.rho, T = m.T;
         const double uu = (double)m.ux * m.ux + (double)m.uy * m.uy + (double)m.uz * m.uz;
         acc[0] += rho;
@@ -321,20 +327,21 @@ __global__ void stats_kernel(const __grid_constant__ KParams p, const P* __restr
         acc[4] += theta * theta;
         acc[5] += T;
         acc[6] += T * T;
-        acc[7] += dux * dux;
+        acc[7] += G[0][0] * G[0][0];
+        acc[8] += wx * wx + wy * wy + wz * wz;
     }
     // block reduction of kStats values (two passes of the 5-value reduction)
+    static_assert(kStats <= 10, "two passes of five values");
     double a5[5] = {acc[0], acc[1], acc[2], acc[3], acc[4]};
     block_sum5(a5, partials + (size_t)kStats * blockIdx.x);
     __syncthreads();
-    double b5[5] = {acc[5], acc[6], acc[7], 0.0, 0.0};
+    double b5[5] = {acc[5], acc[6], acc[7], acc[8], 0.0};
     __shared__ double tail[5];
     block_sum5(b5, tail);
     __syncthreads();
     if (threadIdx.x == 0) {
-        partials[(size_t)kStats * blockIdx.x + 5] = tail[0];
-        partials[(size_t)kStats * blockIdx.x + 6] = tail[1];
-        partials[(size_t)kStats * blockIdx.x + 7] = tail[2];
+#pragma unroll
+        for (int k = 5; k < kStats; ++k) partials[(size_t)kStats * blockIdx.x + k] = tail[k - 5];
     }
 }
 

@@ -179,11 +179,12 @@ def elbm_step_totals(h) -> np.ndarray:
     return out
 
 
-STATS_KEYS = ("rho_mean", "rho_rms", "K", "u_rms", "theta_rms", "T_mean", "T_rms", "dudx2")
+STATS_KEYS = ("rho_mean", "rho_rms", "K", "u_rms", "theta_rms", "T_mean", "T_rms", "dudx2", "omega_rms",
+              "enstrophy")
 
 
 def elbm_turbulence_stats(h) -> dict:
-    out = np.zeros(8)
+    out = np.zeros(len(STATS_KEYS))
     _check(lib().elbm_turbulence_stats(h, out.ctypes.data_as(_dp)), "elbm_turbulence_stats")
     return dict(zip(STATS_KEYS, out.tolist()))
 

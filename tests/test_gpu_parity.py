@@ -341,3 +341,35 @@ def test_shock_vortex_full_size_sampled(E, store, tol):
         assert abs(T[n] - T_o) <= tol * abs(T_o)
         assert np.max(np.abs(u[:, n] - u_o)) <= tol
     g.close()
+
+
+# --------------------------------------------------------------------------
+# isentropic vortex carried by a uniform flow (Euler translation, Sec. III.C vortex)
+# --------------------------------------------------------------------------
+def _circular_centre(d, L):
+    th = 2.0 * math.pi * np.arange(L) / L
+    out = []
+    for w in (d.sum(axis=0), d.sum(axis=1)):
+        ang = math.atan2(float((w * np.sin(th)).sum()), float((w * np.cos(th)).sum()))
+        out.append((ang * L / (2.0 * math.pi)) % L)
+    return out
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_vortex_translation_parity_f64(E, kernel):
+    """Quarter period of the translating vortex (u_y changes sign: FP64 only)."""
+    c = C.isentropic_vortex(L=48, U0=0.1, Ma_v=0.1, r_v=6.0, T0=0.15, mu=0.002)
+    steps = 120
+    ref = oracle_fields(("vortex",), c, steps)
+    assert_parity(gpu_fields(E, c, steps, "f64", kernel), ref, TOL["f64"], ("vortex", kernel))
+
+
+@pytest.mark.parametrize("store", ["f32", "f16dev"])
+def test_vortex_translation_reduced_precision(E, store):
+    """The reduced-precision stores carry the vortex to L/2 + U0 t like the Euler
+    solution (the same property the oracle is pinned to)."""
+    c = C.isentropic_vortex(L=48, U0=0.1, Ma_v=0.1, r_v=6.0, T0=0.15, mu=0.002)
+    L, U0, steps = c.nx, c.extra["U0"], 120
+    rho, _, T = gpu_fields(E, c, steps, store)
+    x, y = _circular_centre(c.T0 - (rho * T).reshape(L, L), L)
+    assert abs(x - (L / 2 + U0 * steps) % L) < 0.1 and abs(y - L / 2) < 0.1

@@ -552,3 +552,43 @@ def test_standing_normal_shock_rankine_hugoniot():
     assert np.mean(rho[dn]) / np.mean(rho[up]) == pytest.approx(r_rho, rel=5e-3)
     assert np.mean(P[dn]) / np.mean(P[up]) == pytest.approx(r_p, rel=5e-3)
     assert np.mean(T[dn]) / np.mean(T[up]) == pytest.approx(r_T, rel=5e-3)
+
+
+# --------------------------------------------------------------------------
+# isentropic vortex carried by a uniform flow (Sec. III.C vortex; Euler translation)
+# --------------------------------------------------------------------------
+def _circular_centre(d, L):
+    """Centre of a positive bump on a periodic L x L grid (circular mean per axis)."""
+    th = 2.0 * math.pi * np.arange(L) / L
+    out = []
+    for w in (d.sum(axis=0), d.sum(axis=1)):
+        ang = math.atan2(float((w * np.sin(th)).sum()), float((w * np.cos(th)).sum()))
+        out.append((ang * L / (2.0 * math.pi)) % L)
+    return out
+
+
+def test_isentropic_vortex_translates_with_the_flow():
+    """The isentropic vortex is a steady solution of the Euler equations; carried by
+    u_x = U0 it translates unchanged.  Its pressure deficit must sit at
+    x = L/2 + U0 t after a quarter period (which tells the direction of advection
+    apart) and back at the centre after a full period, with the profile changed only
+    by viscous decay (mu = 0.002, r_v = 6: bound 1.3x the measured 0.128)."""
+    c = C.isentropic_vortex(L=48, U0=0.1, Ma_v=0.1, r_v=6.0, T0=0.15, mu=0.002)
+    L, U0 = c.nx, c.extra["U0"]
+    s = O.init(params_of(c), c.rho, c.u, c.T)
+
+    def deficit():
+        rho, _, T = O.fields(s)
+        return c.T0 - (rho * T).reshape(L, L)   # far-field pressure rho0 T0 = T0
+
+    d0 = deficit()
+    t1, t2 = int(round(L / (4 * U0))), int(round(L / U0))
+    O.step(s, t1)
+    x1, y1 = _circular_centre(deficit(), L)
+    assert abs(x1 - (L / 2 + U0 * t1) % L) < 0.1
+    assert abs(y1 - L / 2) < 0.1
+    O.step(s, t2 - t1)
+    d2 = deficit()
+    x2, y2 = _circular_centre(d2, L)
+    assert abs(x2 - L / 2) < 0.1 and abs(y2 - L / 2) < 0.1
+    assert np.linalg.norm(d2 - d0) / np.linalg.norm(d0) < 0.17
