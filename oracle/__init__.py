@@ -45,6 +45,7 @@ class _Params(ctypes.Structure):
         ("bc", ctypes.c_int * 6),
         ("deriv", ctypes.c_int),
         ("correction", ctypes.c_int),
+        ("fix_rho", ctypes.c_double), ("fix_u", ctypes.c_double * 3), ("fix_T", ctypes.c_double),
     ]
 
 
@@ -63,6 +64,7 @@ class Params:
     bc: tuple = (0, 0, 0, 0, 0, 0)
     deriv: int = 0
     correction: int = 1
+    fixed: tuple = (0.0, 0.0, 0.0, 0.0, 0.0)   # (rho, u_x, u_y, u_z, T) of fixed-state faces (bc 2)
 
     @property
     def Q(self) -> int:
@@ -80,6 +82,10 @@ class Params:
             s.bc[k] = int(self.bc[k])
         s.deriv = self.deriv
         s.correction = self.correction
+        s.fix_rho = float(self.fixed[0])
+        for a in range(3):
+            s.fix_u[a] = float(self.fixed[1 + a])
+        s.fix_T = float(self.fixed[4])
         return s
 
 

@@ -33,7 +33,11 @@
  *  - omega and omega_1 are node-local, from the local pressure P = rho T;
  *  - boundaries: a periodic axis wraps indices; a zero-gradient face copies the
  *    adjacent interior node (its post-collision populations and its Q~) into the
- *    ghost, i.e. the index is clamped;
+ *    ghost, i.e. the index is clamped; a fixed-state face (a supersonic inflow)
+ *    holds in its ghost the equilibrium populations f^eq, g^eq of a prescribed
+ *    uniform state, which is also their post-collision value (a uniform
+ *    equilibrium state has no gradients and no non-equilibrium part), and that
+ *    state's Q~; a ghost beyond a fixed face on any axis is a fixed ghost;
  *  - D2Q9 is the same product form over x and y, with Cv = 1/(gamma-1).
  */
 #include <math.h>
@@ -50,9 +54,11 @@ typedef struct {
     double gamma;          /* adiabatic exponent, Cv = R/(gamma-1), R = 1            */
     double Pr;             /* Prandtl number, Eq. Pr                                 */
     double mu0, T0, mu_exp;/* mu = mu0 (T/T0)^mu_exp (mu_exp = 0: constant mu)       */
-    int bc[6];             /* faces -x,+x,-y,+y,-z,+z: 0 periodic, 1 zero-gradient   */
+    int bc[6];             /* faces -x,+x,-y,+y,-z,+z: 0 periodic, 1 zero-gradient,
+                              2 fixed state (supersonic inflow)                      */
     int deriv;             /* 0 first-order upwind, 1 second-order central           */
     int correction;        /* 1 extended equilibrium (the method); 0 plain f^eq      */
+    double fix_rho, fix_u[3], fix_T;   /* the state of every fixed-state face        */
 } orc_params;
 
 /* ----------------------------------------------------------------------------
@@ -322,7 +328,12 @@ static int map_axis(int x, int n, int bc_lo, int bc_hi) {
     return x;
 }
 
+/* Node index of (x,y,z) after the boundary maps, or -1 for a ghost beyond a
+ * fixed-state face. */
 static long node_of(const orc_params *p, int x, int y, int z) {
+    const int v[3] = {x, y, z}, n[3] = {p->nx, p->ny, p->nz};
+    for (int a = 0; a < 3; ++a)
+        if ((v[a] < 0 && p->bc[2 * a] == 2) || (v[a] >= n[a] && p->bc[2 * a + 1] == 2)) return -1;
     x = map_axis(x, p->nx, p->bc[0], p->bc[1]);
     y = map_axis(y, p->ny, p->bc[2], p->bc[3]);
     z = map_axis(z, p->nz, p->bc[4], p->bc[5]);
@@ -373,9 +384,11 @@ static double dQ_axis(const orc_params *p, const double *Qt, const double *uvel,
     long np = node_of(p, x + e[0], y + e[1], z + e[2]);
     long nm = node_of(p, x - e[0], y - e[1], z - e[2]);
     const double *q = Qt + a * N;
-    if (p->deriv == 1) return 0.5 * (q[np] - q[nm]);
-    double right = uvel[a * N + n0] > 0.0 ? q[n0] : q[np];   /* Q~ at i+1/2 */
-    double left = uvel[a * N + n0] > 0.0 ? q[nm] : q[n0];    /* Q~ at i-1/2 */
+    const double qfix = anomaly(p->fix_rho, p->fix_u[a], p->fix_T);   /* fixed ghost */
+    const double q0 = q[n0], qp = np < 0 ? qfix : q[np], qm = nm < 0 ? qfix : q[nm];
+    if (p->deriv == 1) return 0.5 * (qp - qm);
+    double right = uvel[a * N + n0] > 0.0 ? q0 : qp;   /* Q~ at i+1/2 */
+    double left = uvel[a * N + n0] > 0.0 ? qm : q0;    /* Q~ at i-1/2 */
     return right - left;
 }
 
@@ -388,6 +401,9 @@ int orc_step(const orc_params *p, double *f, double *g, int nsteps) {
     double *Qt = (double *)malloc(sizeof(double) * 3 * N);
     double *uvel = (double *)malloc(sizeof(double) * 3 * N);
     if (!fpc || !gpc || !Qt || !uvel) { free(fpc); free(gpc); free(Qt); free(uvel); return -1; }
+    double ffix[27], gfix[27];   /* ghost populations of a fixed-state face */
+    orc_fex(p, p->fix_rho, p->fix_u, p->fix_T, 1.0, NULL, ffix);
+    orc_geq(p, p->fix_rho, p->fix_u, p->fix_T, gfix);
 
     for (int s = 0; s < nsteps; ++s) {
         /* 1-2: moments and anomaly at every node */
@@ -408,7 +424,8 @@ int orc_step(const orc_params *p, double *f, double *g, int nsteps) {
             for (int a = 0; a < D; ++a) dQ[a] = dQ_axis(p, Qt, uvel, x, y, z, a);
             orc_collide_node(p, f + n * Q, g + n * Q, dQ, fpc + n * Q, gpc + n * Q, NULL, NULL, NULL);
         }
-        /* 5-6: pull streaming f_i(x) <- f_i^pc(x - c_i), ghosts by index mapping */
+        /* 5-6: pull streaming f_i(x) <- f_i^pc(x - c_i), ghosts by index mapping;
+         * fixed ghosts hold the equilibria of the fixed state */
 #pragma omp parallel for schedule(static)
         for (long n = 0; n < N; ++n) {
             int x = (int)(n % p->nx), y = (int)((n / p->nx) % p->ny), z = (int)(n / ((long)p->nx * p->ny));
@@ -416,8 +433,8 @@ int orc_step(const orc_params *p, double *f, double *g, int nsteps) {
                 int c[3];
                 orc_c(i, D, c);
                 long src = node_of(p, x - c[0], y - c[1], z - c[2]);
-                f[n * Q + i] = fpc[src * Q + i];
-                g[n * Q + i] = gpc[src * Q + i];
+                f[n * Q + i] = src < 0 ? ffix[i] : fpc[src * Q + i];
+                g[n * Q + i] = src < 0 ? gfix[i] : gpc[src * Q + i];
             }
         }
     }

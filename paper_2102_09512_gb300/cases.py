@@ -42,8 +42,9 @@ class Case:
     mu0: float = 1e-3
     T0: float = 0.15
     mu_exp: float = 0.0
-    bc: tuple = (0, 0, 0, 0, 0, 0)
+    bc: tuple = (0, 0, 0, 0, 0, 0)      # per face -x,+x,-y,+y,-z,+z: 0 periodic, 1 zero-gradient, 2 fixed
     extra: dict = field(default_factory=dict)
+    fixed: tuple = (0.0, 0.0, 0.0, 0.0, 0.0)   # (rho, u_x, u_y, u_z, T) of the fixed-state faces
 
     @property
     def N(self) -> int:
@@ -81,14 +82,17 @@ def rankine_hugoniot(Ma: float, gamma: float = 1.4):
 
 def shock_vortex(nx: int = 1024, ny: int = 1024, Ma_s: float = 1.2, Ma_v: float = 0.25,
                  r_v: float = 32.0, Re: float = 800.0, Pr: float = 0.75, gamma: float = 1.4,
-                 T_l: float = 0.05, rho_l: float = 1.0, r_v_mu: float = 60.0) -> Case:
+                 T_l: float = 0.05, rho_l: float = 1.0, r_v_mu: float = 60.0,
+                 inflow: bool = False) -> Case:
     """Standing normal shock at x_s = 8 r_v (left state rho_l, T_l, u = Ma_s sqrt(gamma T_l),
     right state by Rankine-Hugoniot) with an isentropic vortex of Mach Ma_v and radius
     r_v centred at (6 r_v, ny/2) superposed on the local base state.
     mu = rho_l c_s,l r_v_mu / Re: by default the viscosity of the paper's run (r_v = 60,
     Re = 800) is kept when the domain is scaled down; a smaller mu (e.g. Re = 800 on
     r_v = 32) makes the initial shock diverge within a few hundred steps.
-    y periodic, x zero-gradient."""
+    y periodic; x zero-gradient, or with inflow=True the -x face holds the upstream
+    state fixed (a supersonic inflow) and +x stays zero-gradient.  The paper's run is
+    shock_vortex(1680, 1440, r_v=60, inflow=True) (Sec. III.C)."""
     rho, u, T = _empty(2, nx, ny, 1)
     cs_l = math.sqrt(gamma * T_l)
     ux_l = Ma_s * cs_l
@@ -114,8 +118,10 @@ def shock_vortex(nx: int = 1024, ny: int = 1024, Ma_s: float = 1.2, Ma_v: float 
     u[1, 0] = uy
     mu = rho_l * cs_l * r_v_mu / Re
     return Case("shock_vortex", 2, nx, ny, 1, rho, u, T, gamma=gamma, Pr=Pr, mu0=mu, T0=T_l,
-                bc=(1, 1, 0, 0, 0, 0),
-                extra=dict(Ma_s=Ma_s, Ma_v=Ma_v, r_v=r_v, Re=Re, x_s=xs, x_v=xv, y_v=yv, cs_l=cs_l))
+                bc=(2 if inflow else 1, 1, 0, 0, 0, 0),
+                extra=dict(Ma_s=Ma_s, Ma_v=Ma_v, r_v=r_v, Re=Re, x_s=xs, x_v=xv, y_v=yv, cs_l=cs_l,
+                           P_s=rho_l * T_l * r_p, u_s=ux_l * r_u),
+                fixed=(rho_l, ux_l, 0.0, 0.0, T_l))
 
 
 def _central_dx(a: np.ndarray, axis: int) -> np.ndarray:

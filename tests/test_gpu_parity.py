@@ -46,7 +46,7 @@ def E():
 
 def oparams(c, **kw):
     d = dict(D=c.D, nx=c.nx, ny=c.ny, nz=c.nz, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0,
-             mu_exp=c.mu_exp, bc=c.bc)
+             mu_exp=c.mu_exp, bc=c.bc, fixed=c.fixed)
     d.update(kw)
     return O.Params(**d)
 

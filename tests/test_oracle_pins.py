@@ -46,7 +46,7 @@ def read_golden(name):
 
 def params_of(c: C.Case, **kw) -> O.Params:
     d = dict(D=c.D, nx=c.nx, ny=c.ny, nz=c.nz, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0,
-             mu_exp=c.mu_exp, bc=c.bc)
+             mu_exp=c.mu_exp, bc=c.bc, fixed=c.fixed)
     d.update(kw)
     return O.Params(**d)
 
@@ -592,3 +592,52 @@ def test_isentropic_vortex_translates_with_the_flow():
     x2, y2 = _circular_centre(d2, L)
     assert abs(x2 - L / 2) < 0.1 and abs(y2 - L / 2) < 0.1
     assert np.linalg.norm(d2 - d0) / np.linalg.norm(d0) < 0.17
+
+
+# --------------------------------------------------------------------------
+# fixed-state face (supersonic inflow)
+# --------------------------------------------------------------------------
+def test_fixed_state_face_keeps_matching_uniform_flow():
+    """A uniform flow whose fixed-state faces hold its own state is a fixed point
+    (the ghost equilibria are the flow's post-collision populations)."""
+    rho0, u0, T0 = 1.1, (0.3, -0.05, 0.0), 0.12
+    c = C.random_smooth(2, 24, 10, 1, drho=0.0, du=0.0, dT=0.0, rho0=rho0, T0=T0, u0=u0,
+                        bc=(2, 1, 0, 0, 0, 0))
+    p = params_of(c, fixed=(rho0, u0[0], u0[1], u0[2], T0))
+    s = O.init(p, c.rho, c.u, c.T)
+    f0, g0 = s.f.copy(), s.g.copy()
+    O.step(s, 50)
+    assert np.max(np.abs(s.f - f0)) < 1e-14 and np.max(np.abs(s.g - g0)) < 1e-14
+
+
+def test_fixed_state_face_feeds_a_standing_shock():
+    """Sec. III.C with a supersonic inflow: the -x face holds the Ma = 1.2 upstream
+    state, +x is zero-gradient.  The upstream region starts 2 % denser than the fixed
+    state at the same pressure; every wave of a supersonic stream runs downstream, so
+    the inflow replaces that gas by the fixed state (a zero-gradient face would keep
+    it), the standing shock stays at its initial position and the downstream state
+    keeps the Rankine-Hugoniot ratios (normal_shock_M1p2.txt)."""
+    gold = read_golden("normal_shock_M1p2.txt")
+    nx, ny = 300, 2
+    c = C.shock_vortex(nx=nx, ny=ny, Ma_s=1.2, Ma_v=0.0, r_v=nx / 16.0, Re=150.0, Pr=0.75,
+                       r_v_mu=nx / 16.0, inflow=True)
+    assert c.bc[0] == 2
+    upstream = np.arange(nx) < c.extra["x_s"]
+    c.rho[0][:, upstream] *= 1.02
+    c.T[0][:, upstream] /= 1.02
+    s = O.init(params_of(c), c.rho, c.u, c.T)
+    O.step(s, 1500)
+    rho, u, T = O.fields(s)
+    rho = rho.reshape(ny, nx)[0]
+    T = T.reshape(ny, nx)[0]
+    ux = u[0].reshape(ny, nx)[0]
+    xs = c.extra["x_s"]
+    pos = np.argmax(rho > 0.5 * (1.0 + gold["rho2_over_rho1"]))
+    assert abs(pos - xs) <= 2
+    up = slice(0, int(xs) - 30)
+    dn = slice(int(xs) + 30, nx - 20)
+    rho_l, ux_l, _, _, T_l = c.fixed
+    assert np.max(np.abs(rho[up] - rho_l)) < 1e-3 and np.max(np.abs(ux[up] - ux_l)) < 1e-3
+    assert np.max(np.abs(T[up] - T_l)) < 1e-3
+    assert np.mean(rho[dn]) / rho_l == pytest.approx(gold["rho2_over_rho1"], rel=5e-3)
+    assert np.mean(rho[dn] * T[dn]) / (rho_l * T_l) == pytest.approx(gold["p2_over_p1"], rel=5e-3)
