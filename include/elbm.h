@@ -55,8 +55,12 @@ typedef enum { ELBM_D2Q9 = 9, ELBM_D3Q27 = 27 } elbm_lattice;
 
 /* Per face -x,+x,-y,+y,-z,+z.  An axis is periodic on both faces or on neither.
  * Zero-gradient: the ghost node holds a copy of the adjacent interior node (its
- * post-collision populations and its Q~); the paper states no boundary type. */
-typedef enum { ELBM_BC_PERIODIC = 0, ELBM_BC_ZEROGRAD = 1 } elbm_bc;
+ * post-collision populations and its Q~); the paper states no boundary type.
+ * Fixed state (a supersonic inflow, as upstream of the shock in Sec. III.C): the
+ * ghost holds the equilibria f^eq, g^eq of the uniform state fix_rho, fix_u, fix_T
+ * of elbm_params (their own post-collision values) and that state's Q~; D2Q9 only
+ * (ELBM_ERR_UNSUPPORTED for D3Q27). */
+typedef enum { ELBM_BC_PERIODIC = 0, ELBM_BC_ZEROGRAD = 1, ELBM_BC_FIXED = 2 } elbm_bc;
 
 /* Population storage.  F64 and F32 store the populations; F16DEV and BF16DEV store
  * their deviation from the rest state f^eq(rho_ref, 0, T_ref), g^eq(rho_ref, 0, T_ref)
@@ -90,6 +94,9 @@ typedef struct {
     int deriv;           /* elbm_deriv                                                */
     double rho_ref;      /* rest state of the deviation stores (ignored for F64/F32)  */
     double T_ref;
+    double fix_rho;      /* state of the ELBM_BC_FIXED faces (ignored without one):    */
+    double fix_u[3];     /*   density > 0, velocity, temperature > 0                   */
+    double fix_T;
 } elbm_params;
 
 typedef struct elbm_handle elbm_handle;

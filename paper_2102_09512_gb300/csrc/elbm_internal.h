@@ -12,8 +12,31 @@
 
 namespace elbm {
 
+// f^eq and g^eq of a uniform state for D2Q9 in FP64 on the host (Eqs. 27eq, geq_i in
+// the per-axis closed form of the kernels): phi = Psi(u, T + u^2),
+// psi = {(s - o)/2, u^2/2 - s, (s + o)/2} with o = T u + u^3/2, s = T^2 + 5/2 T u^2 + u^4/2,
+// f_i = rho phi_x phi_y, g_i = rho [(Cv T phi_x + psi_x) phi_y + phi_x psi_y].
+inline void host_equilibria_d2q9(double rho, const double u[3], double T, double Cv, double f[9], double g[9]) {
+    double ph[2][3], ps[2][3];
+    for (int a = 0; a < 2; ++a) {
+        const double v = u[a], v2 = v * v, P = T + v2;
+        ph[a][0] = 0.5 * (P - v);
+        ph[a][1] = 1.0 - P;
+        ph[a][2] = 0.5 * (P + v);
+        const double o = T * v + 0.5 * v2 * v, s = T * T + 2.5 * T * v2 + 0.5 * v2 * v2;
+        ps[a][0] = 0.5 * (s - o);
+        ps[a][1] = 0.5 * v2 - s;
+        ps[a][2] = 0.5 * (s + o);
+    }
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) {
+            f[a + 3 * b] = rho * ph[0][a] * ph[1][b];
+            g[a + 3 * b] = rho * ((Cv * T * ph[0][a] + ps[0][a]) * ph[1][b] + ph[0][a] * ps[1][b]);
+        }
+}
+
 // Validates a problem statement and fills the kernel parameters (host only, no CUDA
-// call, no allocation).  Returns ELBM_OK or ELBM_ERR_ARG; *D_out is 2 or 3.
+// call, no allocation).  Returns ELBM_OK, ELBM_ERR_ARG or ELBM_ERR_UNSUPPORTED; *D_out is 2 or 3.
 inline int fill_kparams(const elbm_params& p, KParams& k, int* D_out) {
     auto finite_pos = [](double v) { return std::isfinite(v) && v > 0.0; };
     int D;
@@ -24,8 +47,18 @@ inline int fill_kparams(const elbm_params& p, KParams& k, int* D_out) {
     if (!(std::isfinite(p.gamma) && p.gamma > 1.0)) return ELBM_ERR_ARG;
     if (!finite_pos(p.Pr) || !finite_pos(p.mu0) || !finite_pos(p.T0) || !std::isfinite(p.mu_exp))
         return ELBM_ERR_ARG;
-    for (int f = 0; f < 6; ++f)
-        if (p.bc[f] != ELBM_BC_PERIODIC && p.bc[f] != ELBM_BC_ZEROGRAD) return ELBM_ERR_ARG;
+    bool any_fixed = false;
+    for (int f = 0; f < 6; ++f) {
+        if (p.bc[f] != ELBM_BC_PERIODIC && p.bc[f] != ELBM_BC_ZEROGRAD && p.bc[f] != ELBM_BC_FIXED)
+            return ELBM_ERR_ARG;
+        any_fixed |= p.bc[f] == ELBM_BC_FIXED;
+    }
+    if (any_fixed) {
+        if (!finite_pos(p.fix_rho) || !finite_pos(p.fix_T) || !std::isfinite(p.fix_u[0]) ||
+            !std::isfinite(p.fix_u[1]) || !std::isfinite(p.fix_u[2]))
+            return ELBM_ERR_ARG;
+        if (D != 2) return ELBM_ERR_UNSUPPORTED;
+    }
     for (int a = 0; a < 3; ++a)
         if ((p.bc[2 * a] == ELBM_BC_PERIODIC) != (p.bc[2 * a + 1] == ELBM_BC_PERIODIC)) return ELBM_ERR_ARG;
     if (p.store < ELBM_F64 || p.store > ELBM_BF16DEV) return ELBM_ERR_ARG;
@@ -56,6 +89,24 @@ inline int fill_kparams(const elbm_params& p, KParams& k, int* D_out) {
     k.f_mu0 = (float)p.mu0;
     k.f_invT0 = (float)k.d_invT0;
     k.f_mu_exp = (float)p.mu_exp;
+    if (any_fixed) {
+        // ghosts of the fixed-state faces: f^eq, g^eq and Q~ of the fixed state (D2Q9)
+        k.has_fixed = 1;
+        for (int a = 0; a < 3; ++a) {
+            k.fix_lo[a] = p.bc[2 * a] == ELBM_BC_FIXED;
+            k.fix_hi[a] = p.bc[2 * a + 1] == ELBM_BC_FIXED;
+        }
+        double fe[9], ge[9];
+        host_equilibria_d2q9(p.fix_rho, p.fix_u, p.fix_T, 1.0 / (p.gamma - 1.0), fe, ge);
+        for (int i = 0; i < 9; ++i) {
+            k.fixd[i][0] = fe[i];
+            k.fixd[i][1] = ge[i];
+        }
+        for (int a = 0; a < 3; ++a) {
+            k.fixQd[a] = p.fix_rho * p.fix_u[a] * (1.0 - 3.0 * p.fix_T - p.fix_u[a] * p.fix_u[a]);
+            k.fixQf[a] = (float)k.fixQd[a];
+        }
+    }
     // z segment of the fused D3Q27 kernels: longer for FP32 (one CTA per SM, so
     // fewer prologues per plane matter more), measured at 256^3
     const int tz = p.store == ELBM_F32 ? 64 : 32;
@@ -86,6 +137,15 @@ inline int fill_kparams(const elbm_params& p, KParams& k, int* D_out) {
         k.rest_Pyy = (float)syy;
         k.rest_Pzz = (float)szz;
         k.rest_E = (float)sE;
+    }
+    if (k.has_fixed) {
+        // the same ghosts as raw stored values of the FP32 arithmetic path (deviations
+        // from the rest state for the deviation stores)
+        for (int i = 0; i < 9; ++i) {
+            const double rf = dev ? (double)k.rest2[i].x : 0.0, rg = dev ? (double)k.rest2[i].y : 0.0;
+            k.fixf[i].x = (float)(k.fixd[i][0] - rf);
+            k.fixf[i].y = (float)(k.fixd[i][1] - rg);
+        }
     }
     *D_out = D;
     return ELBM_OK;

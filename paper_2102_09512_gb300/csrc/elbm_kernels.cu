@@ -58,7 +58,27 @@ __device__ __forceinline__ long long node_index(const KParams& p, int x, int y, 
 struct PullRows {
     int row[3][3];   // node index of (0, ys[b], zs[c])
     int xs[3];
+    unsigned gmask;  // bit i: direction i is pulled from beyond a fixed-state face
 };
+
+// Fixed-state faces (D2Q9): is coordinate v of axis a beyond a fixed face, and the
+// ghost values there (the fixed state's equilibria as raw stored values, its Q~).
+__device__ __forceinline__ bool beyond_fixed(const KParams& p, int a, int v, int n) {
+    return (v < 0 && p.fix_lo[a]) || (v >= n && p.fix_hi[a]);
+}
+__device__ __forceinline__ void fixed_pair(const KParams& p, int i, R& f, R& g) {
+    if constexpr (sizeof(R) == 8) {
+        f = p.fixd[i][0];
+        g = p.fixd[i][1];
+    } else {
+        f = p.fixf[i].x;
+        g = p.fixf[i].y;
+    }
+}
+__device__ __forceinline__ R fixed_Q(const KParams& p, int a) {
+    if constexpr (sizeof(R) == 8) return p.fixQd[a];
+    else return p.fixQf[a];
+}
 
 // With PULL = false every direction is read at the node itself (no streaming);
 // that form is used once, to collide the initial state.
@@ -78,6 +98,17 @@ __device__ __forceinline__ void pull_rows(const KParams& p, int x, int y, int z,
 #pragma unroll
         for (int b = 0; b < 3; ++b)
             r.row[b][c] = p.nx * (ys[b] + p.ny * zs[c]);
+    r.gmask = 0;
+    if constexpr (kD == 2 && PULL) {
+        if (p.has_fixed) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    if (beyond_fixed(p, 0, x + 1 - a, p.nx) || beyond_fixed(p, 1, y + 1 - b, p.ny))
+                        r.gmask |= 1u << (a + 3 * b);
+        }
+    }
 }
 
 // Address of the pair of direction i pulled by node r in store s.
@@ -90,6 +121,11 @@ __device__ __forceinline__ void gather(const KParams& p, const P* __restrict__ s
                                        R* f, R* g) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) Cd::dec(*src_ptr(p, src, r, i), f[i], g[i]);
+    if (r.gmask) {   // sources beyond a fixed-state face (the load above read a clamped node)
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            if ((r.gmask >> i) & 1u) fixed_pair(p, i, f[i], g[i]);
+    }
 }
 
 __device__ __forceinline__ void load_local(const KParams& p, const P* __restrict__ pop, long long n, R* f,
@@ -390,9 +426,16 @@ __global__ void collide_kernel(const __grid_constant__ KParams p, const P* __res
         const long long N = p.N;
         const int xm = map_axis(x - 1, p.nx, p.per_x), xp = map_axis(x + 1, p.nx, p.per_x);
         const int ym = map_axis(y - 1, p.ny, p.per_y), yp = map_axis(y + 1, p.ny, p.per_y);
-        const R Dx = dQ(p.deriv, m.ux, qf[node_index(p, xm, y, z)], qf[n], qf[node_index(p, xp, y, z)]);
-        const R Dy = dQ(p.deriv, m.uy, qf[N + node_index(p, x, ym, z)], qf[N + n],
-                        qf[N + node_index(p, x, yp, z)]);
+        R qxm = qf[node_index(p, xm, y, z)], qxp = qf[node_index(p, xp, y, z)];
+        R qym = qf[N + node_index(p, x, ym, z)], qyp = qf[N + node_index(p, x, yp, z)];
+        if (kD == 2 && p.has_fixed) {
+            if (beyond_fixed(p, 0, x - 1, p.nx)) qxm = fixed_Q(p, 0);
+            if (beyond_fixed(p, 0, x + 1, p.nx)) qxp = fixed_Q(p, 0);
+            if (beyond_fixed(p, 1, y - 1, p.ny)) qym = fixed_Q(p, 1);
+            if (beyond_fixed(p, 1, y + 1, p.ny)) qyp = fixed_Q(p, 1);
+        }
+        const R Dx = dQ(p.deriv, m.ux, qxm, qf[n], qxp);
+        const R Dy = dQ(p.deriv, m.uy, qym, qf[N + n], qyp);
         R Dz = R(0);
         if (kD == 3) {
             const int zm = map_axis(z - 1, p.nz, p.per_z), zp = map_axis(z + 1, p.nz, p.per_z);
@@ -473,14 +516,23 @@ __device__ __forceinline__ void fused2d_tile(const KParams& p, const P* __restri
         int hx, hy, sx, sy, axis;
         const int h = tx + TX * ty;
         if (h < 2 * TX + 2 * TY && halo_node<TY>(p, h, x0, y0, xl, yl, hx, hy, sx, sy, axis)) {
-            PullRows r;
-            pull_rows(p, hx, hy, 0, r);
-            R hf[Q], hg[Q];
-            gather(p, src, r, hf, hg);
-            Moments<R> hm;
-            node_moments<kD, R, false, DEV>(hf, hg, p, hm);
-            if (axis == 1) qy[sy][sx] = anomaly(hm.rho, hm.uy, hm.T);
-            else qx[sy][sx] = anomaly(hm.rho, hm.ux, hm.T);
+            R q;
+            // the unmapped halo coordinate is (x0 + sx - 1, y0 + sy - 1) for columns and
+            // (x0 + sx, y0 + sy - 1) for rows
+            if (p.has_fixed && (axis == 1 ? beyond_fixed(p, 1, y0 + sy - 1, p.ny)
+                                          : beyond_fixed(p, 0, x0 + sx - 1, p.nx))) {
+                q = fixed_Q(p, axis);
+            } else {
+                PullRows r;
+                pull_rows(p, hx, hy, 0, r);
+                R hf[Q], hg[Q];
+                gather(p, src, r, hf, hg);
+                Moments<R> hm;
+                node_moments<kD, R, false, DEV>(hf, hg, p, hm);
+                q = anomaly(hm.rho, axis == 1 ? hm.uy : hm.ux, hm.T);
+            }
+            if (axis == 1) qy[sy][sx] = q;
+            else qx[sy][sx] = q;
         }
     }
     __syncthreads();

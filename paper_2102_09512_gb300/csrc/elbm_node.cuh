@@ -35,6 +35,12 @@ struct KParams {
     float rest_rho, rest_Pxx, rest_Pyy, rest_Pzz, rest_E;   // their moment sums
     // The same parameters precomputed in both arithmetic types, so that no kernel
     // converts or divides a double per node (the FP64 pipe of GB300 is narrow).
+    // fixed-state faces (D2Q9): flags per axis face and the ghost values
+    int has_fixed, fix_lo[3], fix_hi[3];
+    double fixd[9][2];           // ghost pair (f_i, g_i), FP64 store representation
+    float2 fixf[9];              // the same as raw stored values of the FP32 path
+    double fixQd[3];             // Q~_aaa of the fixed state
+    float fixQf[3];
     int powlaw;                                            // mu_exp != 0
     double d_Cv, d_invT0;
     float f_gm1, f_Cv, f_Pr, f_mu0, f_invT0, f_mu_exp;

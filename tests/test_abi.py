@@ -85,3 +85,17 @@ def test_unbound_handle_is_rejected(L):
     h = L.elbm_create(L.make_params(2, 16, 16, 1))
     assert L.elbm_step(h, 1) == L.ELBM_ERR_ARG
     L.elbm_destroy(h)
+
+
+def test_fixed_state_faces_are_validated(L):
+    fixed = (1.0, 0.3, 0.0, 0.0, 0.05)
+    h = L.elbm_create(L.make_params(2, 32, 16, 1, bc=(2, 1, 0, 0, 0, 0), fixed=fixed))
+    L.elbm_destroy(h)
+    with pytest.raises(L.ElbmError) as ei:   # the fixed state must be physical
+        L.elbm_create(L.make_params(2, 32, 16, 1, bc=(2, 1, 0, 0, 0, 0), fixed=(0.0, 0.3, 0.0, 0.0, 0.05)))
+    assert ei.value.code == L.ELBM_ERR_ARG
+    with pytest.raises(L.ElbmError) as ei:   # D2Q9 only
+        L.elbm_create(L.make_params(3, 16, 16, 16, bc=(2, 1, 0, 0, 0, 0), fixed=fixed))
+    assert ei.value.code == L.ELBM_ERR_UNSUPPORTED
+    with pytest.raises(L.ElbmError):          # a fixed face cannot pair with a periodic one
+        L.elbm_create(L.make_params(2, 32, 16, 1, bc=(2, 0, 0, 0, 0, 0), fixed=fixed))

@@ -37,7 +37,7 @@ def small_cases():
         C.random_smooth(2, 45, 23, 1, seed=1, mu0=0.01),
         C.sod(nx=64, ny=9, mu=0.015),
         C.random_smooth(2, 37, 29, 1, seed=2, mu0=0.02, bc=(1, 1, 1, 1, 0, 0)),
-        C.shock_vortex(nx=96, ny=40, r_v=5.0, Ma_s=1.3),
+        C.shock_vortex(nx=96, ny=40, r_v=5.0, Ma_s=1.3, inflow=True),   # fixed-state -x face
         C.random_smooth(2, 33, 65, 1, seed=3, mu0=0.01),
     ]
 

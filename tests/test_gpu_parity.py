@@ -373,3 +373,19 @@ def test_vortex_translation_reduced_precision(E, store):
     rho, _, T = gpu_fields(E, c, steps, store)
     x, y = _circular_centre(c.T0 - (rho * T).reshape(L, L), L)
     assert abs(x - (L / 2 + U0 * steps) % L) < 0.1 and abs(y - L / 2) < 0.1
+
+
+# --------------------------------------------------------------------------
+# fixed-state face: supersonic inflow upstream of the shock (Sec. III.C)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("store,kernel", [("f64", 0), ("f64", 1), ("f32", 0), ("f16dev", 0)])
+def test_shock_vortex_inflow_parity(E, store, kernel):
+    """The shock-vortex case with the -x face holding the upstream state fixed, on a
+    grid ragged against the tiles (150 x 70, r_v = 8), 150 steps, against the oracle.
+    u_y changes sign around the vortex, so the reduced-precision stores are held to
+    10x their one-signed bounds, as in test_shock_vortex_parity."""
+    c = C.shock_vortex(nx=150, ny=70, r_v=8.0, Ma_s=1.2, inflow=True)
+    ref = oracle_fields(("shock_vortex_inflow",), c, 150)
+    got = gpu_fields(E, c, 150, store, kernel)
+    tol = TOL["f64"] if store == "f64" else 10 * TOL[store]
+    assert_parity(got, ref, tol, (store, kernel))
