@@ -46,6 +46,7 @@ class _Params(ctypes.Structure):
         ("deriv", ctypes.c_int),
         ("correction", ctypes.c_int),
         ("fix_rho", ctypes.c_double), ("fix_u", ctypes.c_double * 3), ("fix_T", ctypes.c_double),
+        ("eos", ctypes.c_int), ("cv", ctypes.c_double * 4),
     ]
 
 
@@ -65,6 +66,7 @@ class Params:
     deriv: int = 0
     correction: int = 1
     fixed: tuple = (0.0, 0.0, 0.0, 0.0, 0.0)   # (rho, u_x, u_y, u_z, T) of fixed-state faces (bc 2)
+    cv: tuple = None   # None: constant Cv = 1/(gamma-1); else Cv(T) = cv[0] + cv[1] T + cv[2] T^2 + cv[3] T^3
 
     @property
     def Q(self) -> int:
@@ -86,6 +88,9 @@ class Params:
         for a in range(3):
             s.fix_u[a] = float(self.fixed[1 + a])
         s.fix_T = float(self.fixed[4])
+        s.eos = 0 if self.cv is None else 1
+        for k in range(4):
+            s.cv[k] = 0.0 if self.cv is None else float(self.cv[k])
         return s
 
 

@@ -38,7 +38,10 @@
  *    uniform state, which is also their post-collision value (a uniform
  *    equilibrium state has no gradients and no non-equilibrium part), and that
  *    state's Q~; a ghost beyond a fixed face on any axis is a fixed ghost;
- *  - D2Q9 is the same product form over x and y, with Cv = 1/(gamma-1).
+ *  - D2Q9 is the same product form over x and y, with Cv = 1/(gamma-1);
+ *  - the caloric equation of state is either constant Cv = 1/(gamma-1) or a cubic
+ *    Cv(T); U(T) enters g^eq as the constant term of the generating function and T is
+ *    recovered from U by Newton's method.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -59,6 +62,9 @@ typedef struct {
     int deriv;             /* 0 first-order upwind, 1 second-order central           */
     int correction;        /* 1 extended equilibrium (the method); 0 plain f^eq      */
     double fix_rho, fix_u[3], fix_T;   /* the state of every fixed-state face        */
+    int eos;               /* 0: constant Cv = 1/(gamma-1); 1: Cv(T) = cv[0] + cv[1] T
+                              + cv[2] T^2 + cv[3] T^3 (a general caloric ideal gas)   */
+    double cv[4];
 } orc_params;
 
 /* ----------------------------------------------------------------------------
@@ -152,11 +158,36 @@ static double poly_eval(const poly3 *p, const double u[3]) {
     return s;
 }
 
-/* Generating function E = U + u^2/2 with U = Cv T, constant Cv (Eqs. U, E). */
+/* Caloric equation of state (Eq. U, reference temperature 0, R = 1): the specific
+ * heat Cv(T), the internal energy U(T) = int_0^T Cv dT, and its inverse. */
+static double Cv_of_T(const orc_params *p, double T) {
+    if (p->eos == 0) return 1.0 / (p->gamma - 1.0);
+    return p->cv[0] + T * (p->cv[1] + T * (p->cv[2] + T * p->cv[3]));
+}
+
+static double U_of_T(const orc_params *p, double T) {
+    if (p->eos == 0) return T / (p->gamma - 1.0);
+    return T * (p->cv[0] + T * (p->cv[1] / 2.0 + T * (p->cv[2] / 3.0 + T * p->cv[3] / 4.0)));
+}
+
+/* T with U(T) = U: Newton's method on the monotone U (Cv > 0), from the estimate with
+ * Cv(0), to a relative step of 1e-15. */
+static double T_of_U(const orc_params *p, double U) {
+    if (p->eos == 0) return U * (p->gamma - 1.0);
+    double T = U / p->cv[0];
+    for (int k = 0; k < 100; ++k) {
+        const double dT = (U_of_T(p, T) - U) / Cv_of_T(p, T);
+        T -= dT;
+        if (fabs(dT) <= 1e-15 * fabs(T)) break;
+    }
+    return T;
+}
+
+/* Generating function E = U(T) + u^2/2 (Eqs. U, E); the operators act on u only, so
+ * U(T) enters as the constant term. */
 static void energy_poly(const orc_params *p, double T, poly3 *E) {
     memset(E, 0, sizeof(*E));
-    const double Cv = 1.0 / (p->gamma - 1.0);
-    E->c[0][0][0] = Cv * T;
+    E->c[0][0][0] = U_of_T(p, T);
     E->c[2][0][0] = 0.5;
     E->c[0][2][0] = 0.5;
     if (p->D == 3) E->c[0][0][2] = 0.5;
@@ -243,8 +274,7 @@ static void node_moments(const orc_params *p, const double *f, const double *g, 
     double u2 = 0;
     for (int a = 0; a < 3; ++a) { m->u[a] = j[a] / rho; u2 += m->u[a] * m->u[a]; }
     m->E = rE / rho;
-    const double Cv = 1.0 / (p->gamma - 1.0);
-    m->T = (m->E - 0.5 * u2) / Cv;
+    m->T = T_of_U(p, m->E - 0.5 * u2);
     memcpy(m->P, P, sizeof(P));
 }
 

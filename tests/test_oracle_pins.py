@@ -641,3 +641,85 @@ def test_fixed_state_face_feeds_a_standing_shock():
     assert np.max(np.abs(T[up] - T_l)) < 1e-3
     assert np.mean(rho[dn]) / rho_l == pytest.approx(gold["rho2_over_rho1"], rel=5e-3)
     assert np.mean(rho[dn] * T[dn]) / (rho_l * T_l) == pytest.approx(gold["p2_over_p1"], rel=5e-3)
+
+
+# --------------------------------------------------------------------------
+# general caloric equation of state (Eqs. U, E, qeq, Req)
+# --------------------------------------------------------------------------
+CV_POLY = (1.0, 4.0, -4.0, 5.0)   # Cv(T) = 1 + 4T - 4T^2 + 5T^3, increasing, > 0 for T >= 0
+
+
+def _U_poly(T, cv=CV_POLY):
+    return T * (cv[0] + T * (cv[1] / 2 + T * (cv[2] / 3 + T * cv[3] / 4)))
+
+
+def _Cv_poly(T, cv=CV_POLY):
+    return cv[0] + T * (cv[1] + T * (cv[2] + T * cv[3]))
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_caloric_constant_cv_is_the_constant_gamma_model(D):
+    """Cv(T) = 1/(gamma-1) written as a polynomial gives the constant-gamma model."""
+    c = C.random_smooth(D, 9, 7, 5, seed=3, mu0=0.01, u0=(0.05, -0.03, 0.02))
+    a = O.init(params_of(c), c.rho, c.u, c.T)
+    b = O.init(params_of(c, cv=(1.0 / (c.gamma - 1.0), 0.0, 0.0, 0.0)), c.rho, c.u, c.T)
+    O.step(a, 20)
+    O.step(b, 20)
+    for x, y in zip(O.fields(a), O.fields(b)):
+        assert np.max(np.abs(x - y)) <= 1e-13 * np.max(np.abs(y))
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_caloric_energy_moments(D):
+    """With Cv(T) cubic: sum g^eq = rho (U(T) + u^2/2) with U = int_0^T Cv dT (Eqs. U, E),
+    q^eq = (H + u^2/2) rho u and R^eq = (H + u^2/2) P^eq + P u u with H = U + T
+    (Mayer's relation, R = 1; Eqs. qeq, Req); the fields return the same T."""
+    p = O.Params(D=D, cv=CV_POLY)
+    c = O.velocities(D)
+    for rho, u, T in STATES:
+        u = u.copy()
+        if D == 2:
+            u[2] = 0
+        g = O.geq(p, rho, u, T)
+        f = O.feq(p, rho, u, T)
+        u2 = float(u @ u)
+        assert lattice_moment(c, g, 0, 0, 0) == pytest.approx(rho * (_U_poly(T) + 0.5 * u2), rel=1e-12)
+        h = _U_poly(T) + T + 0.5 * u2
+        for a in range(D):
+            e = [0, 0, 0]
+            e[a] = 1
+            assert lattice_moment(c, g, *e) == pytest.approx(h * rho * u[a], rel=1e-12)
+            for b in range(D):
+                e2 = [0, 0, 0]
+                e2[a] += 1
+                e2[b] += 1
+                Peq = rho * T * (a == b) + rho * u[a] * u[b]
+                ref = h * Peq + rho * T * u[a] * u[b]
+                assert lattice_moment(c, g, *e2) == pytest.approx(ref, rel=1e-12, abs=1e-15)
+        s = O.State(p, f[None, :].copy(), g[None, :].copy())
+        s.p = O.Params(D=D, nx=1, ny=1, nz=1, cv=CV_POLY)
+        _, _, T_back = O.fields(s)
+        assert T_back[0] == pytest.approx(T, rel=1e-13)
+
+
+def test_caloric_sound_speed_and_attenuation():
+    """Linear acoustics of the caloric gas at T0: c_s^2 = gamma(T0) T0 with
+    gamma(T0) = Cp(T0)/Cv(T0) = (Cv(T0) + 1)/Cv(T0), and the NSF attenuation with that
+    Cv in the bulk viscosity (Eq. bulkvisc) and Cp in the conduction term."""
+    T0, mu, L = 0.15, 0.01, 64
+    Cv = _Cv_poly(T0)
+    gamma = (Cv + 1.0) / Cv
+    c = C.sound_wave(D=2, L=L, U0=0.0, mu=mu, T0=T0, A=1e-5, gamma=gamma)
+    p = params_of(c, cv=CV_POLY)
+    ts, a = _track(c, p, "rho", 1500, 10)
+    sel = ts >= 200
+    Gam = -np.polyfit(ts[sel], np.log(np.abs(a[sel])), 1)[0]
+    freq = -np.polyfit(ts[sel], np.unwrap(np.angle(a))[sel], 1)[0]
+    k = 2 * math.pi / L
+    zeta = (2.0 / 3.0 - 1.0 / Cv) * mu
+    alpha = mu / c.Pr
+    Gam_nsf = 0.5 * k * k * ((4.0 / 3.0 * mu + zeta) + (gamma - 1.0) * alpha)
+    assert freq / k == pytest.approx(math.sqrt(gamma * T0), rel=2e-3)
+    assert Gam == pytest.approx(Gam_nsf, rel=0.02)
+    # the same wave with the constant-gamma model of gamma = 1.4 runs at another speed
+    assert abs(math.sqrt(gamma * T0) / math.sqrt(1.4 * T0) - 1.0) > 0.05
