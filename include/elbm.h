@@ -67,6 +67,12 @@ typedef enum { ELBM_BC_PERIODIC = 0, ELBM_BC_ZEROGRAD = 1, ELBM_BC_FIXED = 2 } e
  * rounded to nearest even, with FP32 arithmetic. */
 typedef enum { ELBM_F64 = 0, ELBM_F32 = 1, ELBM_F16DEV = 2, ELBM_BF16DEV = 3 } elbm_store;
 
+/* Caloric equation of state of the ideal gas (Eqs. U, E; R = 1, reference temperature
+ * 0): constant Cv = 1/(gamma - 1), or Cv(T) = cv[0] + cv[1] T + cv[2] T^2 + cv[3] T^3
+ * with U(T) = int_0^T Cv dT (gamma then unused; cv[0] > 0 and Cv must stay positive
+ * over the run's temperatures).  T is recovered from U by Newton's method. */
+typedef enum { ELBM_EOS_GAMMA = 0, ELBM_EOS_CV_POLY = 1 } elbm_eos;
+
 /* Spatial derivative of Q~_aaa: first-order upwind (the paper's choice, Sec. III.A)
  * or second-order central (its comparison variant). */
 typedef enum { ELBM_DERIV_UPWIND = 0, ELBM_DERIV_CENTRAL = 1 } elbm_deriv;
@@ -97,6 +103,8 @@ typedef struct {
     double fix_rho;      /* state of the ELBM_BC_FIXED faces (ignored without one):    */
     double fix_u[3];     /*   density > 0, velocity, temperature > 0                   */
     double fix_T;
+    int eos;             /* elbm_eos                                                  */
+    double cv[4];        /* Cv(T) coefficients for ELBM_EOS_CV_POLY                    */
 } elbm_params;
 
 typedef struct elbm_handle elbm_handle;

@@ -45,6 +45,7 @@ class Case:
     bc: tuple = (0, 0, 0, 0, 0, 0)      # per face -x,+x,-y,+y,-z,+z: 0 periodic, 1 zero-gradient, 2 fixed
     extra: dict = field(default_factory=dict)
     fixed: tuple = (0.0, 0.0, 0.0, 0.0, 0.0)   # (rho, u_x, u_y, u_z, T) of the fixed-state faces
+    cv: tuple = None   # None: Cv = 1/(gamma-1); else Cv(T) = cv[0] + cv[1] T + cv[2] T^2 + cv[3] T^3
 
     @property
     def N(self) -> int:

@@ -12,11 +12,18 @@
 
 namespace elbm {
 
+// Internal energy U(T) = int_0^T Cv dT of the problem's caloric equation of state.
+inline double host_U(const elbm_params& p, double T) {
+    if (p.eos == ELBM_EOS_CV_POLY)
+        return T * (p.cv[0] + T * (p.cv[1] / 2.0 + T * (p.cv[2] / 3.0 + T * p.cv[3] / 4.0)));
+    return T / (p.gamma - 1.0);
+}
+
 // f^eq and g^eq of a uniform state for D2Q9 in FP64 on the host (Eqs. 27eq, geq_i in
 // the per-axis closed form of the kernels): phi = Psi(u, T + u^2),
 // psi = {(s - o)/2, u^2/2 - s, (s + o)/2} with o = T u + u^3/2, s = T^2 + 5/2 T u^2 + u^4/2,
-// f_i = rho phi_x phi_y, g_i = rho [(Cv T phi_x + psi_x) phi_y + phi_x psi_y].
-inline void host_equilibria_d2q9(double rho, const double u[3], double T, double Cv, double f[9], double g[9]) {
+// f_i = rho phi_x phi_y, g_i = rho [(U phi_x + psi_x) phi_y + phi_x psi_y] with U = U(T).
+inline void host_equilibria_d2q9(double rho, const double u[3], double T, double U, double f[9], double g[9]) {
     double ph[2][3], ps[2][3];
     for (int a = 0; a < 2; ++a) {
         const double v = u[a], v2 = v * v, P = T + v2;
@@ -31,7 +38,7 @@ inline void host_equilibria_d2q9(double rho, const double u[3], double T, double
     for (int b = 0; b < 3; ++b)
         for (int a = 0; a < 3; ++a) {
             f[a + 3 * b] = rho * ph[0][a] * ph[1][b];
-            g[a + 3 * b] = rho * ((Cv * T * ph[0][a] + ps[0][a]) * ph[1][b] + ph[0][a] * ps[1][b]);
+            g[a + 3 * b] = rho * ((U * ph[0][a] + ps[0][a]) * ph[1][b] + ph[0][a] * ps[1][b]);
         }
 }
 
@@ -46,6 +53,10 @@ inline int fill_kparams(const elbm_params& p, KParams& k, int* D_out) {
     if (p.nx < 1 || p.ny < 1 || p.nz < 1 || (D == 2 && p.nz != 1)) return ELBM_ERR_ARG;
     if (!(std::isfinite(p.gamma) && p.gamma > 1.0)) return ELBM_ERR_ARG;
     if (!finite_pos(p.Pr) || !finite_pos(p.mu0) || !finite_pos(p.T0) || !std::isfinite(p.mu_exp))
+        return ELBM_ERR_ARG;
+    if (p.eos != ELBM_EOS_GAMMA && p.eos != ELBM_EOS_CV_POLY) return ELBM_ERR_ARG;
+    if (p.eos == ELBM_EOS_CV_POLY &&
+        (!finite_pos(p.cv[0]) || !std::isfinite(p.cv[1]) || !std::isfinite(p.cv[2]) || !std::isfinite(p.cv[3])))
         return ELBM_ERR_ARG;
     bool any_fixed = false;
     for (int f = 0; f < 6; ++f) {
@@ -82,6 +93,13 @@ inline int fill_kparams(const elbm_params& p, KParams& k, int* D_out) {
     k.deriv = p.deriv;
     k.powlaw = p.mu_exp != 0.0;
     k.d_Cv = 1.0 / (p.gamma - 1.0);
+    k.eos = p.eos == ELBM_EOS_CV_POLY;
+    for (int j = 0; j < 4; ++j) {
+        k.cvd[j] = k.eos ? p.cv[j] : 0.0;
+        k.Ud[j] = k.cvd[j] / (j + 1);
+        k.cvf[j] = (float)k.cvd[j];
+        k.Uf[j] = (float)k.Ud[j];
+    }
     k.d_invT0 = 1.0 / p.T0;
     k.f_gm1 = (float)k.gm1;
     k.f_Cv = (float)k.d_Cv;
@@ -97,7 +115,7 @@ inline int fill_kparams(const elbm_params& p, KParams& k, int* D_out) {
             k.fix_hi[a] = p.bc[2 * a + 1] == ELBM_BC_FIXED;
         }
         double fe[9], ge[9];
-        host_equilibria_d2q9(p.fix_rho, p.fix_u, p.fix_T, 1.0 / (p.gamma - 1.0), fe, ge);
+        host_equilibria_d2q9(p.fix_rho, p.fix_u, p.fix_T, host_U(p, p.fix_T), fe, ge);
         for (int i = 0; i < 9; ++i) {
             k.fixd[i][0] = fe[i];
             k.fixd[i][1] = ge[i];
@@ -115,7 +133,7 @@ inline int fill_kparams(const elbm_params& p, KParams& k, int* D_out) {
         // Rest state f^eq(rho_ref, 0, T_ref), g^eq(rho_ref, 0, T_ref): with u = 0 the
         // per-axis factors are phi = (T/2, 1-T, T/2) and psi = (T^2/2, -T^2, T^2/2).
         const int Q = D == 3 ? 27 : 9;
-        const double T0 = p.T_ref, Cv = 1.0 / (p.gamma - 1.0);
+        const double T0 = p.T_ref, U0 = host_U(p, T0);
         const double phi[3] = {0.5 * T0, 1.0 - T0, 0.5 * T0};
         const double psi[3] = {0.5 * T0 * T0, -T0 * T0, 0.5 * T0 * T0};
         double srho = 0, sxx = 0, syy = 0, szz = 0, sE = 0;
@@ -123,7 +141,7 @@ inline int fill_kparams(const elbm_params& p, KParams& k, int* D_out) {
             const int a = i % 3, b = (i / 3) % 3, c = D == 3 ? i / 9 : 1;
             const double pz = D == 3 ? phi[c] : 1.0, sz = D == 3 ? psi[c] : 0.0;
             k.rest2[i].x = (float)(p.rho_ref * phi[a] * phi[b] * pz);
-            k.rest2[i].y = (float)(p.rho_ref * ((Cv * T0 * phi[a] + psi[a]) * phi[b] * pz +
+            k.rest2[i].y = (float)(p.rho_ref * ((U0 * phi[a] + psi[a]) * phi[b] * pz +
                                                 phi[a] * (psi[b] * pz + phi[b] * sz)));
             // moment sums of the stored (rounded) rest values
             srho += k.rest2[i].x;

@@ -234,7 +234,7 @@ __global__ void init_kernel(const __grid_constant__ KParams p, const double* __r
         bad = !(r > R(0)) || !(t > R(0)) || !isfinite(r) || !isfinite(t) || !isfinite(ux) ||
               !isfinite(uy) || !isfinite(uz);
         R f[Q], g[Q];
-        equilibria<kD, R>(r, ux, uy, uz, t, par<R>(p.d_Cv, p.f_Cv), f, g);
+        equilibria<kD, R>(r, ux, uy, uz, t, U_of_T(t, p), f, g);
         if constexpr (DEV) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {

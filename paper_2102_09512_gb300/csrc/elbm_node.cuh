@@ -41,6 +41,10 @@ struct KParams {
     float2 fixf[9];              // the same as raw stored values of the FP32 path
     double fixQd[3];             // Q~_aaa of the fixed state
     float fixQf[3];
+    // caloric equation of state: 0 constant Cv (d_Cv, gm1); 1 Cv(T) cubic, U(T) quartic
+    int eos;
+    double cvd[4], Ud[4];        // Cv(T) = sum cvd[k] T^k, U(T) = T sum Ud[k] T^k (Ud[k] = cvd[k]/(k+1))
+    float cvf[4], Uf[4];
     int powlaw;                                            // mu_exp != 0
     double d_Cv, d_invT0;
     float f_gm1, f_Cv, f_Pr, f_mu0, f_invT0, f_mu_exp;
@@ -123,6 +127,29 @@ __device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double qpow(double a, double b) { return pow(a, b); }
 __device__ __forceinline__ float qpow(float a, float b) { return __powf(a, b); }
+
+// ---------------------------------------------------------------------------
+// Caloric equation of state (Eqs. U, E; R = 1): U(T) = int_0^T Cv dT and its inverse
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R cubic(const double* cd, const float* cf, R T) {
+    return par<R>(cd[0], cf[0]) + T * (par<R>(cd[1], cf[1]) + T * (par<R>(cd[2], cf[2]) + T * par<R>(cd[3], cf[3])));
+}
+template <typename R>
+__device__ __forceinline__ R U_of_T(R T, const KParams& p) {
+    if (!p.eos) return T * par<R>(p.d_Cv, p.f_Cv);
+    return T * cubic<R>(p.Ud, p.Uf, T);
+}
+// T from U: constant Cv directly; otherwise Newton's method on the increasing U(T)
+// from T = U / Cv(0), a fixed 8 iterations (enough for T <= 1 with the stated Cv).
+template <typename R>
+__device__ __forceinline__ R T_of_U(R U, const KParams& p) {
+    if (!p.eos) return U * par<R>(p.gm1, p.f_gm1);
+    R T = U / par<R>(p.cvd[0], p.cvf[0]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) T -= (T * cubic<R>(p.Ud, p.Uf, T) - U) / cubic<R>(p.cvd, p.cvf, T);
+    return T;
+}
 
 // ---------------------------------------------------------------------------
 // Moments
@@ -215,7 +242,7 @@ __device__ __forceinline__ void finish_moments(R rho, R jx, R jy, R jz, R rE, co
     m.uy = jy * inv;
     m.uz = jz * inv;
     const R u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
-    m.T = (rE * inv - R(0.5) * u2) * par<R>(p.gm1, p.f_gm1);
+    m.T = T_of_U(rE * inv - R(0.5) * u2, p);
 }
 
 // All moments of one node: f_moments, g_energy, finish_moments.
@@ -285,13 +312,13 @@ __device__ __forceinline__ void gfactors(R u, R T, R phi[3], R ps[3]) {
 // Equilibria f^eq and g^eq of (rho, u, T) into f, g (full populations; used for
 // initialisation).
 template <int D, typename R>
-__device__ __forceinline__ void equilibria(R rho, R ux, R uy, R uz, R T, R Cv, R* f, R* g) {
+__device__ __forceinline__ void equilibria(R rho, R ux, R uy, R uz, R T, R U, R* f, R* g) {
     R X[3], Y[3], Z[3], sx[3], sy[3], sz[3];
     gfactors(ux, T, X, sx);
     gfactors(uy, T, Y, sy);
     if (D == 3) gfactors(uz, T, Z, sz);
     else { Z[0] = Z[2] = 0; Z[1] = 1; sz[0] = sz[1] = sz[2] = 0; }
-    const R CvT = Cv * T;
+    const R CvT = U;   // U(T): Cv T for constant Cv
 #pragma unroll
     for (int c = 0; c < Lat<D>::NC; ++c) {
         const int cc = (D == 3) ? c : 1;
@@ -355,13 +382,12 @@ struct Relax {
         omw = R(1) - w;
         wr = w * rho;
         // g-equilibrium
-        const R Cv = par<R>(p.d_Cv, p.f_Cv);
         R sx[3];
         gfactors(ux, T, gx, sx);
         gfactors(uy, T, gy, sy);
         if (D == 3) gfactors(uz, T, gz, sz);
         else { gz[0] = gz[2] = 0; gz[1] = 1; sz[0] = sz[1] = sz[2] = 0; }
-        const R CvT = Cv * T;
+        const R CvT = U_of_T(T, p);   // U(T) (Cv T for constant Cv)
 #pragma unroll
         for (int a = 0; a < 3; ++a) ax[a] = CvT * gx[a] + sx[a];
         omw1 = R(1) - w1;

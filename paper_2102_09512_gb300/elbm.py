@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libelbm.so")
 ELBM_OK, ELBM_ERR_ARG, ELBM_ERR_UNSUPPORTED, ELBM_ERR_CUDA, ELBM_ERR_NONPHYSICAL, ELBM_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 ELBM_D2Q9, ELBM_D3Q27 = 9, 27
 ELBM_BC_PERIODIC, ELBM_BC_ZEROGRAD, ELBM_BC_FIXED = 0, 1, 2
+ELBM_EOS_GAMMA, ELBM_EOS_CV_POLY = 0, 1
 ELBM_F64, ELBM_F32, ELBM_F16DEV, ELBM_BF16DEV = 0, 1, 2, 3
 ELBM_DERIV_UPWIND, ELBM_DERIV_CENTRAL = 0, 1
 ELBM_KERNEL_FUSED, ELBM_KERNEL_TWOPASS, ELBM_KERNEL_FUSED_REREAD = 0, 1, 2
@@ -47,6 +48,7 @@ class elbm_params(ctypes.Structure):
         ("deriv", ctypes.c_int),
         ("rho_ref", ctypes.c_double), ("T_ref", ctypes.c_double),
         ("fix_rho", ctypes.c_double), ("fix_u", ctypes.c_double * 3), ("fix_T", ctypes.c_double),
+        ("eos", ctypes.c_int), ("cv", ctypes.c_double * 4),
     ]
 
 
@@ -302,8 +304,9 @@ def elbm_ensemble_destroy(e):
 # ---------------------------------------------------------------------------
 def make_params(lattice, nx, ny, nz=1, gamma=1.4, Pr=0.71, mu0=1e-3, T0=0.15, mu_exp=0.0,
                 bc=(0, 0, 0, 0, 0, 0), store=ELBM_F32, deriv=ELBM_DERIV_UPWIND,
-                rho_ref=1.0, T_ref=None, fixed=(0.0, 0.0, 0.0, 0.0, 0.0)) -> elbm_params:
-    """elbm_params of a problem; fixed = (rho, u_x, u_y, u_z, T) of the ELBM_BC_FIXED faces."""
+                rho_ref=1.0, T_ref=None, fixed=(0.0, 0.0, 0.0, 0.0, 0.0), cv=None) -> elbm_params:
+    """elbm_params of a problem; fixed = (rho, u_x, u_y, u_z, T) of the ELBM_BC_FIXED faces;
+    cv = None for constant Cv = 1/(gamma-1), else the coefficients of a cubic Cv(T)."""
     p = elbm_params()
     p.lattice = ELBM_D3Q27 if lattice in (3, 27, ELBM_D3Q27) else ELBM_D2Q9
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
@@ -318,6 +321,9 @@ def make_params(lattice, nx, ny, nz=1, gamma=1.4, Pr=0.71, mu0=1e-3, T0=0.15, mu
     for a in range(3):
         p.fix_u[a] = float(fixed[1 + a])
     p.fix_T = float(fixed[4])
+    p.eos = ELBM_EOS_GAMMA if cv is None else ELBM_EOS_CV_POLY
+    for k in range(4):
+        p.cv[k] = 0.0 if cv is None else float(cv[k])
     return p
 
 
@@ -351,7 +357,8 @@ class Solver:
         rho_ref = float(np.mean(case.rho)) if rho_ref is None else rho_ref
         T_ref = float(np.mean(case.T)) if T_ref is None else T_ref
         p = make_params(case.D, case.nx, case.ny, case.nz, case.gamma, case.Pr, case.mu0, case.T0,
-                        case.mu_exp, case.bc, store, deriv, rho_ref, T_ref, getattr(case, "fixed", (0,) * 5))
+                        case.mu_exp, case.bc, store, deriv, rho_ref, T_ref, getattr(case, "fixed", (0,) * 5),
+                        getattr(case, "cv", None))
         s = cls(p, **kw)
         s.set_fields(case.rho, case.u, case.T)
         return s
@@ -458,7 +465,8 @@ class Ensemble:
         ps = []
         for c in cases:
             ps.append(make_params(2, c.nx, c.ny, 1, c.gamma, c.Pr, c.mu0, c.T0, c.mu_exp, c.bc, store, 0,
-                                  float(np.mean(c.rho)), float(np.mean(c.T)), getattr(c, "fixed", (0,) * 5)))
+                                  float(np.mean(c.rho)), float(np.mean(c.T)), getattr(c, "fixed", (0,) * 5),
+                                  getattr(c, "cv", None)))
         ens = cls(ps, **kw)
         for k, c in enumerate(cases):
             ens.set_fields(k, c.rho, c.u, c.T)

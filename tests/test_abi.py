@@ -99,3 +99,17 @@ def test_fixed_state_faces_are_validated(L):
     assert ei.value.code == L.ELBM_ERR_UNSUPPORTED
     with pytest.raises(L.ElbmError):          # a fixed face cannot pair with a periodic one
         L.elbm_create(L.make_params(2, 32, 16, 1, bc=(2, 0, 0, 0, 0, 0), fixed=fixed))
+
+
+def test_caloric_eos_is_validated(L):
+    h = L.elbm_create(L.make_params(3, 16, 16, 16, cv=(1.0, 4.0, -4.0, 5.0)))
+    L.elbm_destroy(h)
+    for cv in ((0.0, 1.0, 0.0, 0.0), (1.0, float("nan"), 0.0, 0.0)):
+        with pytest.raises(L.ElbmError) as ei:
+            L.elbm_create(L.make_params(2, 16, 16, 1, cv=cv))
+        assert ei.value.code == L.ELBM_ERR_ARG
+    p = L.make_params(2, 16, 16, 1)
+    p.eos = 7
+    with pytest.raises(L.ElbmError) as ei:
+        L.elbm_create(p)
+    assert ei.value.code == L.ELBM_ERR_ARG

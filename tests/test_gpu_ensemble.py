@@ -107,7 +107,7 @@ def test_instance_matches_oracle(E):
     for k in (1, 3):
         c = cs[k]
         p = O.Params(D=2, nx=c.nx, ny=c.ny, nz=1, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0, mu_exp=c.mu_exp,
-                     bc=c.bc, fixed=c.fixed)
+                     bc=c.bc, fixed=c.fixed, cv=c.cv)
         s = O.init(p, c.rho, c.u, c.T)
         O.step(s, 25)
         for a, b in zip(ens.fields(k), O.fields(s)):

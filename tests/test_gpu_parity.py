@@ -46,7 +46,7 @@ def E():
 
 def oparams(c, **kw):
     d = dict(D=c.D, nx=c.nx, ny=c.ny, nz=c.nz, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0,
-             mu_exp=c.mu_exp, bc=c.bc, fixed=c.fixed)
+             mu_exp=c.mu_exp, bc=c.bc, fixed=c.fixed, cv=c.cv)
     d.update(kw)
     return O.Params(**d)
 
@@ -389,3 +389,21 @@ def test_shock_vortex_inflow_parity(E, store, kernel):
     got = gpu_fields(E, c, 150, store, kernel)
     tol = TOL["f64"] if store == "f64" else 10 * TOL[store]
     assert_parity(got, ref, tol, (store, kernel))
+
+
+# --------------------------------------------------------------------------
+# general caloric equation of state (Eqs. U, E): cubic Cv(T)
+# --------------------------------------------------------------------------
+CV_POLY = (1.0, 4.0, -4.0, 5.0)
+
+
+@pytest.mark.parametrize("D,kernel", [(2, 0), (2, 1), (3, 0), (3, 1), (3, 2)])
+@pytest.mark.parametrize("store", list(TOL))
+def test_caloric_eos_parity(E, D, kernel, store):
+    """Cv(T) = 1 + 4T - 4T^2 + 5T^3: every store and schedule against the oracle (the
+    one-signed flow of the cases above, 60 steps)."""
+    c = (CASES_2D if D == 2 else CASES_3D)["periodic"]()
+    c.cv = CV_POLY
+    steps = 60
+    ref = oracle_fields(("caloric", D), c, steps)
+    assert_parity(gpu_fields(E, c, steps, store, kernel), ref, TOL[store], (D, kernel, store))

@@ -46,7 +46,7 @@ def read_golden(name):
 
 def params_of(c: C.Case, **kw) -> O.Params:
     d = dict(D=c.D, nx=c.nx, ny=c.ny, nz=c.nz, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0,
-             mu_exp=c.mu_exp, bc=c.bc, fixed=c.fixed)
+             mu_exp=c.mu_exp, bc=c.bc, fixed=c.fixed, cv=c.cv)
     d.update(kw)
     return O.Params(**d)
 
