@@ -78,6 +78,8 @@ struct elbm_ensemble {
         a.tiles_x = (const int*)(aux + a_tx[tyi]);
         a.n = n;
         a.ntiles = tile_start[tyi][n];
+        a.caloric = 0;
+        for (const KParams& k : kp) a.caloric |= k.eos;
         return a;
     }
     void drop_graphs() {

@@ -189,6 +189,7 @@ struct EnsembleArgs {
     const int* tile_start;      // [n+1] prefix sums of the instances' tile counts
     const int* tiles_x;         // [n] tiles per row of instance k
     int n, ntiles;
+    int caloric;                // some instance has a Cv(T) model (selects the kernel form)
 };
 
 // Launchers for one (lattice, store) combination.  Each returns the first CUDA

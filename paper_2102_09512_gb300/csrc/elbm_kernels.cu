@@ -490,7 +490,7 @@ __device__ __forceinline__ bool halo_node(const KParams& p, int h, int x0, int y
 // collides and stores.  One launch per step, no intermediate field in HBM.  The tile
 // body is shared by the per-lattice kernel and the persistent ensemble kernel;
 // `partial` (may be null) receives the tile's totals.
-template <int TY>
+template <int TY, bool CAL>
 __device__ __forceinline__ void fused2d_tile(const KParams& p, const P* __restrict__ src, P* __restrict__ dst,
                                              int bx, int by, double* __restrict__ partial,
                                              int* __restrict__ status) {
@@ -508,7 +508,7 @@ __device__ __forceinline__ void fused2d_tile(const KParams& p, const P* __restri
         PullRows r;
         pull_rows(p, x, y, 0, r);
         gather(p, src, r, f, g);
-        node_moments<kD, R, true, DEV>(f, g, p, m);
+        node_moments<kD, R, true, DEV, CAL>(f, g, p, m);
         qx[ty][tx + 1] = anomaly(m.rho, m.ux, m.T);
         qy[ty + 1][tx] = anomaly(m.rho, m.uy, m.T);
     }
@@ -528,7 +528,7 @@ __device__ __forceinline__ void fused2d_tile(const KParams& p, const P* __restri
                 R hf[Q], hg[Q];
                 gather(p, src, r, hf, hg);
                 Moments<R> hm;
-                node_moments<kD, R, false, DEV>(hf, hg, p, hm);
+                node_moments<kD, R, false, DEV, CAL>(hf, hg, p, hm);
                 q = anomaly(hm.rho, axis == 1 ? hm.uy : hm.ux, hm.T);
             }
             if (axis == 1) qy[sy][sx] = q;
@@ -547,7 +547,7 @@ __device__ __forceinline__ void fused2d_tile(const KParams& p, const P* __restri
         node_totals(m, m.rE, v);
 #pragma unroll
         for (int k = 0; k < 5; ++k) tot[k] = (double)v[k];
-        collide<kD, R, DEV>(f, g, m, Dx, Dy, R(0), p);
+        collide<kD, R, DEV, CAL>(f, g, m, Dx, Dy, R(0), p);
         store_node(p, dst, node_index(p, x, y, 0), f, g);
     }
     flag_if(bad, status);
@@ -555,11 +555,11 @@ __device__ __forceinline__ void fused2d_tile(const KParams& p, const P* __restri
     __syncthreads();   // the shared arrays are reused by the next tile of a persistent CTA
 }
 
-template <int TY>
+template <int TY, bool CAL>
 __global__ void __launch_bounds__(TX * TY)
 fused2d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* __restrict__ dst,
                double* __restrict__ partials, int* __restrict__ status) {
-    fused2d_tile<TY>(p, src, dst, blockIdx.x, blockIdx.y, partials + 5 * (blockIdx.x + gridDim.x * blockIdx.y),
+    fused2d_tile<TY, CAL>(p, src, dst, blockIdx.x, blockIdx.y, partials + 5 * (blockIdx.x + gridDim.x * blockIdx.y),
                      status);
 }
 
@@ -567,7 +567,7 @@ fused2d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* 
 // (instance k owns tiles [tile_start[k], tile_start[k+1]), tiles_x[k] per row); CTA
 // b processes tiles b, b + gridDim.x, ...  Instance k's populations start at element
 // offset[k] of both stores; its parameters are params[k].  No totals are kept.
-template <int TY>
+template <int TY, bool CAL>
 __global__ void __launch_bounds__(TX * TY)
 ensemble2d_kernel(const EnsembleArgs a, const P* __restrict__ src, P* __restrict__ dst, int* __restrict__ status) {
     __shared__ int s_start[kMaxEnsemble + 1];
@@ -582,18 +582,19 @@ ensemble2d_kernel(const EnsembleArgs a, const P* __restrict__ src, P* __restrict
         const int local = t - s_start[k];
         const int bx = local % s_tx[k], by = local / s_tx[k];
         const long long off = a.offset[k];
-        fused2d_tile<TY>(a.params[k], src + off, dst + off, bx, by, nullptr, status);
+        fused2d_tile<TY, CAL>(a.params[k], src + off, dst + off, bx, by, nullptr, status);
     }
 }
 
 // Q~_zzz of the node (x, y, z) by a direct gather (used once per z segment).
+template <bool CAL>
 __device__ __forceinline__ R direct_anomaly_z(const KParams& p, const P* __restrict__ src, int x, int y, int z) {
     PullRows r;
     pull_rows(p, x, y, z, r);
     R f[Q], g[Q];
     gather(p, src, r, f, g);
     Moments<R> m;
-    node_moments<kD, R, false, DEV>(f, g, p, m);
+    node_moments<kD, R, false, DEV, CAL>(f, g, p, m);
     return anomaly(m.rho, m.uz, m.T);
 }
 
@@ -640,7 +641,7 @@ struct PipeBytes {
     static constexpr size_t value = Pipe<TY, NB>::smem_bytes;
 };
 
-template <int TY, int NB, int MINB, bool EARLY, int DD>
+template <int TY, int NB, int MINB, bool EARLY, int DD, bool CAL>
 __global__ void __launch_bounds__(TX * TY, MINB)
 fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPlanes pl,
                const P* __restrict__ src, double* __restrict__ partials, int* __restrict__ status) {
@@ -690,7 +691,7 @@ fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPla
         R f[Q], g[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], f[i], g[i]);
-        node_moments<kD, R, decltype(full)::value, DEV>(f, g, p, m);
+        node_moments<kD, R, decltype(full)::value, DEV, CAL>(f, g, p, m);
     };
     using Full = std::true_type;
     using Lite = std::false_type;
@@ -701,7 +702,7 @@ fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPla
 
     // prologue: Q~_zzz below the segment, planes zb and zb+1 in flight, moments of zb
     R qz_prev = R(0), qz_cur = R(0), qz_next = R(0);
-    if (active) qz_prev = direct_anomaly_z(p, src, x, y, map_axis(zb - 1, p.nz, p.per_z));
+    if (active) qz_prev = direct_anomaly_z<CAL>(p, src, x, y, map_axis(zb - 1, p.nz, p.per_z));
     issue_plane(zb, 0, true);
     issue_plane(map_axis(zb + 1, p.nz, p.per_z), 1 % NB, zb + 1 < ze);
     Moments<R> m_cur, m_next;
@@ -774,7 +775,7 @@ fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPla
             node_totals(m_cur, m_cur.rE, v);
             acc.add(v);
             // collide and store pair by pair, decoding each just before its update
-            Relax<kD, R, DEV> rx;
+            Relax<kD, R, DEV, CAL> rx;
             rx.init(m_cur, Dx, Dy, Dz, p);
             const unsigned n = (unsigned)node_index(p, x, y, z);
 #pragma unroll
@@ -798,7 +799,7 @@ fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPla
 
 // D3Q27 without plane buffers: for plane z it computes Q~ of plane z+1 (tile + halo)
 // from a first gather, then gathers plane z again (an L2 hit) to collide it.
-template <int TY>
+template <int TY, bool CAL>
 __global__ void __launch_bounds__(TX * TY, 2)
 fused3d_reread_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* __restrict__ dst,
                       double* __restrict__ partials, int* __restrict__ status) {
@@ -822,7 +823,7 @@ fused3d_reread_kernel(const __grid_constant__ KParams p, const P* __restrict__ s
             R f[Q], g[Q];
             gather(p, src, r, f, g);
             Moments<R> m;
-            node_moments<kD, R, false, DEV>(f, g, p, m);
+            node_moments<kD, R, false, DEV, CAL>(f, g, p, m);
             if (with_xy) {
                 qx[b][ty][tx + 1] = anomaly(m.rho, m.ux, m.T);
                 qy[b][ty + 1][tx] = anomaly(m.rho, m.uy, m.T);
@@ -835,7 +836,7 @@ fused3d_reread_kernel(const __grid_constant__ KParams p, const P* __restrict__ s
             R f[Q], g[Q];
             gather(p, src, r, f, g);
             Moments<R> m;
-            node_moments<kD, R, false, DEV>(f, g, p, m);
+            node_moments<kD, R, false, DEV, CAL>(f, g, p, m);
             if (haxis == 1) qy[b][hsy][hsx] = anomaly(m.rho, m.uy, m.T);
             else qx[b][hsy][hsx] = anomaly(m.rho, m.ux, m.T);
         }
@@ -859,7 +860,7 @@ fused3d_reread_kernel(const __grid_constant__ KParams p, const P* __restrict__ s
             R f[Q], g[Q];
             gather(p, src, r, f, g);
             Moments<R> m;
-            node_moments<kD, R, true, DEV>(f, g, p, m);
+            node_moments<kD, R, true, DEV, CAL>(f, g, p, m);
             bad |= nonphysical(m);
             const R Dx = dQ(p.deriv, m.ux, qx[b][ty][tx], qx[b][ty][tx + 1], qx[b][ty][tx + 2]);
             const R Dy = dQ(p.deriv, m.uy, qy[b][ty][tx], qy[b][ty + 1][tx], qy[b][ty + 2][tx]);
@@ -867,7 +868,7 @@ fused3d_reread_kernel(const __grid_constant__ KParams p, const P* __restrict__ s
             R v[5];
             node_totals(m, m.rE, v);
             acc.add(v);
-            collide<kD, R, DEV>(f, g, m, Dx, Dy, Dz, p);
+            collide<kD, R, DEV, CAL>(f, g, m, Dx, Dy, Dz, p);
             store_node(p, dst, node_index(p, x, y, z), f, g);
         }
         qz_prev = qz_cur;
@@ -962,18 +963,19 @@ cudaError_t launch_twopass(const KParams& p, const void* src, void* dst, void* q
     return cudaGetLastError();
 }
 
-// A template so that the branch of the other lattice is never instantiated.
-template <int DD>
-cudaError_t launch_fused(const KParams& p, const void* src, void* dst, double* partials, int* nblocks,
-                         int* status, cudaStream_t s, long long* launches, bool reread) {
+// A template so that the branch of the other lattice is never instantiated; CAL as in
+// the kernels (the caloric form only for handles with a Cv(T) model).
+template <int DD, bool CAL>
+cudaError_t launch_fused_cal(const KParams& p, const void* src, void* dst, double* partials, int* status,
+                             cudaStream_t s, bool reread) {
     const dim3 grid = fused_grid(p);
     if constexpr (DD == 2) {
-        fused2d_kernel<kTY2><<<grid, dim3(TX, kTY2), 0, s>>>(p, (const P*)src, (P*)dst, partials, status);
+        fused2d_kernel<kTY2, CAL><<<grid, dim3(TX, kTY2), 0, s>>>(p, (const P*)src, (P*)dst, partials, status);
     } else {
         bool launched = false;
         if constexpr (kPipe) {
             if (!reread) {
-                auto kern = fused3d_kernel<kTY3, kNB, kMinB, kEarly, DD>;
+                auto kern = fused3d_kernel<kTY3, kNB, kMinB, kEarly, DD, CAL>;
                 // the dynamic shared-memory limit is a per-function attribute; setting it
                 // again is cheap and keeps this correct for every device of the process
                 cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -989,12 +991,21 @@ cudaError_t launch_fused(const KParams& p, const void* src, void* dst, double* p
             }
         }
         if (!launched)
-            fused3d_reread_kernel<kTY3><<<grid, dim3(TX, kTY3), 0, s>>>(p, (const P*)src, (P*)dst, partials,
-                                                                         status);
+            fused3d_reread_kernel<kTY3, CAL><<<grid, dim3(TX, kTY3), 0, s>>>(p, (const P*)src, (P*)dst, partials,
+                                                                              status);
     }
-    ++*launches;
-    *nblocks = (int)(grid.x * grid.y * grid.z);
     return cudaGetLastError();
+}
+
+template <int DD>
+cudaError_t launch_fused(const KParams& p, const void* src, void* dst, double* partials, int* nblocks,
+                         int* status, cudaStream_t s, long long* launches, bool reread) {
+    const cudaError_t e = p.eos ? launch_fused_cal<DD, true>(p, src, dst, partials, status, s, reread)
+                                : launch_fused_cal<DD, false>(p, src, dst, partials, status, s, reread);
+    ++*launches;
+    const dim3 grid = fused_grid(p);
+    *nblocks = (int)(grid.x * grid.y * grid.z);
+    return e;
 }
 
 cudaError_t launch_fused_default(const KParams& p, const void* src, void* dst, double* partials, int* nblocks,
@@ -1011,9 +1022,17 @@ cudaError_t launch_fused_reread(const KParams& p, const void* src, void* dst, do
 cudaError_t launch_ensemble(const EnsembleArgs& a, const void* src, void* dst, int* status, int ty, int grid,
                             cudaStream_t s, long long* launches) {
     if constexpr (kD == 2) {
-        if (ty == 4) ensemble2d_kernel<4><<<grid, dim3(TX, 4), 0, s>>>(a, (const P*)src, (P*)dst, status);
-        else if (ty == 16) ensemble2d_kernel<16><<<grid, dim3(TX, 16), 0, s>>>(a, (const P*)src, (P*)dst, status);
-        else ensemble2d_kernel<8><<<grid, dim3(TX, 8), 0, s>>>(a, (const P*)src, (P*)dst, status);
+        if (a.caloric) {
+            if (ty == 4) ensemble2d_kernel<4, true><<<grid, dim3(TX, 4), 0, s>>>(a, (const P*)src, (P*)dst, status);
+            else if (ty == 16)
+                ensemble2d_kernel<16, true><<<grid, dim3(TX, 16), 0, s>>>(a, (const P*)src, (P*)dst, status);
+            else ensemble2d_kernel<8, true><<<grid, dim3(TX, 8), 0, s>>>(a, (const P*)src, (P*)dst, status);
+        } else {
+            if (ty == 4) ensemble2d_kernel<4, false><<<grid, dim3(TX, 4), 0, s>>>(a, (const P*)src, (P*)dst, status);
+            else if (ty == 16)
+                ensemble2d_kernel<16, false><<<grid, dim3(TX, 16), 0, s>>>(a, (const P*)src, (P*)dst, status);
+            else ensemble2d_kernel<8, false><<<grid, dim3(TX, 8), 0, s>>>(a, (const P*)src, (P*)dst, status);
+        }
         ++*launches;
         return cudaGetLastError();
     } else {
@@ -1026,9 +1045,11 @@ int ensemble_occupancy(int ty) {
     int nb = 0;
     if constexpr (kD == 2) {
         cudaError_t e;
-        if (ty == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ensemble2d_kernel<4>, TX * 4, 0);
-        else if (ty == 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ensemble2d_kernel<16>, TX * 16, 0);
-        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ensemble2d_kernel<8>, TX * 8, 0);
+        // the constant-gamma form (the caloric one differs by a few registers at most)
+        if (ty == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ensemble2d_kernel<4, false>, TX * 4, 0);
+        else if (ty == 16)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ensemble2d_kernel<16, false>, TX * 16, 0);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ensemble2d_kernel<8, false>, TX * 8, 0);
         if (e != cudaSuccess) return 0;
     }
     return nb;
@@ -1056,13 +1077,13 @@ template <int DD>
 int fused_occupancy_impl() {
     int n = 0;
     if constexpr (DD == 3 && kPipe) {
-        auto kern = fused3d_kernel<kTY3, kNB, kMinB, kEarly, DD>;
+        auto kern = fused3d_kernel<kTY3, kNB, kMinB, kEarly, DD, false>;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PipeCfg::smem_bytes) !=
                 cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX * kTY3, PipeCfg::smem_bytes) != cudaSuccess)
             return 0;
     } else if constexpr (DD == 3) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused3d_reread_kernel<kTY3>, TX * kTY3, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused3d_reread_kernel<kTY3, false>, TX * kTY3, 0) !=
             cudaSuccess)
             return 0;
     }

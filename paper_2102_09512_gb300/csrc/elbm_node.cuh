@@ -135,16 +135,18 @@ template <typename R>
 __device__ __forceinline__ R cubic(const double* cd, const float* cf, R T) {
     return par<R>(cd[0], cf[0]) + T * (par<R>(cd[1], cf[1]) + T * (par<R>(cd[2], cf[2]) + T * par<R>(cd[3], cf[3])));
 }
-template <typename R>
+// CAL = false compiles the constant-Cv model only (the kernels launch that form when
+// the handle's model is constant gamma); CAL = true branches on the handle's model.
+template <typename R, bool CAL = true>
 __device__ __forceinline__ R U_of_T(R T, const KParams& p) {
-    if (!p.eos) return T * par<R>(p.d_Cv, p.f_Cv);
+    if (!CAL || !p.eos) return T * par<R>(p.d_Cv, p.f_Cv);
     return T * cubic<R>(p.Ud, p.Uf, T);
 }
 // T from U: constant Cv directly; otherwise Newton's method on the increasing U(T)
 // from T = U / Cv(0), a fixed 8 iterations (enough for T <= 1 with the stated Cv).
-template <typename R>
+template <typename R, bool CAL = true>
 __device__ __forceinline__ R T_of_U(R U, const KParams& p) {
-    if (!p.eos) return U * par<R>(p.gm1, p.f_gm1);
+    if (!CAL || !p.eos) return U * par<R>(p.gm1, p.f_gm1);
     R T = U / par<R>(p.cvd[0], p.cvf[0]);
 #pragma unroll
     for (int k = 0; k < 8; ++k) T -= (T * cubic<R>(p.Ud, p.Uf, T) - U) / cubic<R>(p.cvd, p.cvf, T);
@@ -233,7 +235,7 @@ __device__ __forceinline__ R g_energy(const R* g, const KParams& p) {
 }
 
 // u = j / rho and T from E = Cv T + u^2/2.
-template <typename R>
+template <typename R, bool CAL = true>
 __device__ __forceinline__ void finish_moments(R rho, R jx, R jy, R jz, R rE, const KParams& p, Moments<R>& m) {
     const R inv = qdiv(R(1), rho);
     m.rho = rho;
@@ -242,16 +244,16 @@ __device__ __forceinline__ void finish_moments(R rho, R jx, R jy, R jz, R rE, co
     m.uy = jy * inv;
     m.uz = jz * inv;
     const R u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
-    m.T = T_of_U(rE * inv - R(0.5) * u2, p);
+    m.T = T_of_U<R, CAL>(rE * inv - R(0.5) * u2, p);
 }
 
 // All moments of one node: f_moments, g_energy, finish_moments.
-template <int D, typename R, bool FULL, bool DEV>
+template <int D, typename R, bool FULL, bool DEV, bool CAL = true>
 __device__ __forceinline__ void node_moments(const R* f, const R* g, const KParams& p, Moments<R>& m) {
     R rho, jx, jy, jz, P6[6];
     f_moments<D, R, FULL, DEV>(f, p, rho, jx, jy, jz, P6);
     const R rE = g_energy<D, R, DEV>(g, p);
-    finish_moments(rho, jx, jy, jz, rE, p, m);
+    finish_moments<R, CAL>(rho, jx, jy, jz, rE, p, m);
     if (FULL) {
         m.Pxx = P6[0]; m.Pyy = P6[1]; m.Pzz = P6[2];
         m.Pxy = P6[3]; m.Pxz = P6[4]; m.Pyz = P6[5];
@@ -361,7 +363,7 @@ __device__ __forceinline__ R rate_w1(R w, const KParams& p) {
 // q* - q^eq = u.(P - P^eq + div Q~ / 2) with P^eq = rho T I + rho u u and
 // div Q~ = diag(D), and g_i += (omega - omega_1)(g^eq_i - g*_i) =
 // -(omega - omega_1) c_i.(q* - q^eq) / 2.  m must carry the pressure tensor.
-template <int D, typename R, bool DEV>
+template <int D, typename R, bool DEV, bool CAL = true>
 struct Relax {
     R omw, omw1, w, w1;
     R X[3], Y[3], Z[3], wr;                      // f^ex factors
@@ -387,7 +389,7 @@ struct Relax {
         gfactors(uy, T, gy, sy);
         if (D == 3) gfactors(uz, T, gz, sz);
         else { gz[0] = gz[2] = 0; gz[1] = 1; sz[0] = sz[1] = sz[2] = 0; }
-        const R CvT = U_of_T(T, p);   // U(T) (Cv T for constant Cv)
+        const R CvT = U_of_T<R, CAL>(T, p);   // U(T) (Cv T for constant Cv)
 #pragma unroll
         for (int a = 0; a < 3; ++a) ax[a] = CvT * gx[a] + sx[a];
         omw1 = R(1) - w1;
@@ -440,10 +442,10 @@ struct Relax {
 };
 
 // One collision in place on the raw stored values f, g.
-template <int D, typename R, bool DEV>
+template <int D, typename R, bool DEV, bool CAL = true>
 __device__ __forceinline__ void collide(R* f, R* g, const Moments<R>& m, R Dx, R Dy, R Dz,
                                         const KParams& p) {
-    Relax<D, R, DEV> r;
+    Relax<D, R, DEV, CAL> r;
     r.init(m, Dx, Dy, Dz, p);
 #pragma unroll
     for (int i = 0; i < Lat<D>::Q; ++i) {

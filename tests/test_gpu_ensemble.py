@@ -33,12 +33,14 @@ def E():
 
 
 def small_cases():
+    caloric = C.random_smooth(2, 33, 65, 1, seed=3, mu0=0.01)
+    caloric.cv = (1.0, 4.0, -4.0, 5.0)   # a cubic Cv(T) instance among constant-gamma ones
     return [
         C.random_smooth(2, 45, 23, 1, seed=1, mu0=0.01),
         C.sod(nx=64, ny=9, mu=0.015),
         C.random_smooth(2, 37, 29, 1, seed=2, mu0=0.02, bc=(1, 1, 1, 1, 0, 0)),
         C.shock_vortex(nx=96, ny=40, r_v=5.0, Ma_s=1.3, inflow=True),   # fixed-state -x face
-        C.random_smooth(2, 33, 65, 1, seed=3, mu0=0.01),
+        caloric,
     ]
 
 
@@ -104,7 +106,7 @@ def test_instance_matches_oracle(E):
     cs = small_cases()
     ens = E.Ensemble.from_cases(cs, store="f64")
     ens.step(25)
-    for k in (1, 3):
+    for k in (1, 3, 4):
         c = cs[k]
         p = O.Params(D=2, nx=c.nx, ny=c.ny, nz=1, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0, mu_exp=c.mu_exp,
                      bc=c.bc, fixed=c.fixed, cv=c.cv)
