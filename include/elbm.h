@@ -151,10 +151,12 @@ int elbm_step_totals(elbm_handle *h, double out[5]);
 /* Turbulence statistics of the current state (paper Sec. III.D), volume averages
  * over all nodes, FP64: out = {<rho>, rho_rms, K = <rho u.u>/2, u_rms = sqrt(<u.u>/D),
  * theta_rms = sqrt(<(div u)^2>), <T>, T_rms, <(d u_x/d x)^2>,
- * omega_rms = sqrt(<|omega|^2>), enstrophy = <|omega|^2>/2} with omega = curl u;
- * derivatives by second-order central differences (ghosts from the boundary map).
- * out holds 10 doubles (caller-owned).  Synchronises. */
-int elbm_turbulence_stats(elbm_handle *h, double out[10]);
+ * omega_rms = sqrt(<|omega|^2>), enstrophy = <|omega|^2>/2,
+ * dissipation = <mu(T) |omega|^2>, lambda = sqrt(<u_x^2>/<(d u_x/d x)^2>),
+ * Re_lambda = <rho> u_rms lambda / mu0} with omega = curl u; derivatives by
+ * second-order central differences (ghosts from the boundary map).  out holds 13
+ * doubles (caller-owned).  Synchronises. */
+int elbm_turbulence_stats(elbm_handle *h, double out[13]);
 
 /* Selects the kernel schedule (elbm_kernel).  Results agree to rounding. */
 int elbm_set_kernel(elbm_handle *h, int kernel);

@@ -57,7 +57,7 @@ const Ops* pick_ops(int D, int store) {
 }
 
 // Compensated FP64 sum over nb partial vectors of `width` values (width <= kMaxWidth).
-constexpr int kMaxWidth = 10;   // widest partial vector: step totals 5, statistics kStatsSums
+constexpr int kMaxWidth = 12;   // widest partial vector: step totals 5, statistics kStatsSums
 static_assert(kStatsSums <= kMaxWidth, "finalize width");
 
 __global__ void finalize_kernel(const double* __restrict__ partials, int nb, int width, double* __restrict__ out) {
@@ -269,7 +269,7 @@ int elbm_conservation(elbm_handle* h, double out[5]) {
     return finalize_to_host(h, query_partials(h), nb, out);
 }
 
-int elbm_turbulence_stats(elbm_handle* h, double out[10]) {
+int elbm_turbulence_stats(elbm_handle* h, double out[13]) {
     if (!h || !h->bound || !out) return ELBM_ERR_ARG;
     int nb = 0;
     double* part = query_partials(h);   // kStatsSums values x (<= max_blocks) CTAs
@@ -290,6 +290,11 @@ int elbm_turbulence_stats(elbm_handle* h, double out[10]) {
     out[7] = sums[7] / N;                                        // <(d u_x/d x)^2>
     out[8] = std::sqrt(sums[8] / N);                             // omega_rms = sqrt(<|omega|^2>)
     out[9] = 0.5 * sums[8] / N;                                  // enstrophy = <|omega|^2>/2
+    out[10] = sums[10] / N;                                      // dissipation <mu |omega|^2>
+    // Taylor microscale and its Reynolds number (Eq. Taylor_Re, with the square root)
+    const double lam = sums[7] > 0.0 ? std::sqrt(sums[9] / sums[7]) : 0.0;
+    out[11] = lam;                                               // lambda = sqrt(<u_x^2>/<(d u_x/d x)^2>)
+    out[12] = mrho * out[3] * lam / h->prm.mu0;                  // Re_lambda = <rho> u_rms lambda / mu0
     return ELBM_OK;
 }
 

@@ -195,7 +195,7 @@ struct EnsembleArgs {
 // Launchers for one (lattice, store) combination.  Each returns the first CUDA
 // error it meets and adds the number of kernels it launched to *launches.
 // Per-CTA partial sums of the turbulence statistics (stats_kernel, elbm_turbulence_stats).
-constexpr int kStatsSums = 9;
+constexpr int kStatsSums = 11;
 
 struct Ops {
     int D, store;

@@ -321,14 +321,14 @@ __device__ __forceinline__ void node_velocity(const KParams& p, const P* __restr
 }
 
 // Turbulence statistics of the current state (one FP64 partial vector per CTA):
-// sums of rho, rho^2, rho u.u, u.u, theta^2, T, T^2, (d u_x / d x)^2 and |omega|^2,
-// with the velocity gradient by second-order central differences (boundary nodes use
-// the ghost values of the boundary map): dilatation theta = div u, vorticity
-// omega = curl u.
+// sums of rho, rho^2, rho u.u, u.u, theta^2, T, T^2, (d u_x / d x)^2, |omega|^2, u_x^2
+// and mu(T) |omega|^2, with the velocity gradient by second-order central differences
+// (boundary nodes use the ghost values of the boundary map): dilatation
+// theta = div u, vorticity omega = curl u, mu = mu0 (T/T0)^mu_exp (Eq. mu law).
 constexpr int kStats = kStatsSums;
 __global__ void stats_kernel(const __grid_constant__ KParams p, const P* __restrict__ pop,
                              double* __restrict__ partials) {
-    double acc[kStats] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double acc[kStats] = {};
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < p.N;
          n += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((long long)p.nx * p.ny));
@@ -363,21 +363,25 @@ __global__ void stats_kernel(const __grid_constant__ KParams p, const P* __restr
         acc[4] += theta * theta;
         acc[5] += T;
         acc[6] += T * T;
+        const double w2 = wx * wx + wy * wy + wz * wz;
+        const double mu = p.mu_exp != 0.0 ? p.mu0 * pow(T / p.T0, p.mu_exp) : p.mu0;
         acc[7] += G[0][0] * G[0][0];
-        acc[8] += wx * wx + wy * wy + wz * wz;
+        acc[8] += w2;
+        acc[9] += (double)m.ux * m.ux;
+        acc[10] += mu * w2;
     }
-    // block reduction of kStats values (two passes of the 5-value reduction)
-    static_assert(kStats <= 10, "two passes of five values");
-    double a5[5] = {acc[0], acc[1], acc[2], acc[3], acc[4]};
-    block_sum5(a5, partials + (size_t)kStats * blockIdx.x);
-    __syncthreads();
-    double b5[5] = {acc[5], acc[6], acc[7], acc[8], 0.0};
+    // block reduction of kStats values, five at a time
+    static_assert(kStats <= 15, "three passes of five values");
     __shared__ double tail[5];
-    block_sum5(b5, tail);
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    for (int base = 0; base < kStats; base += 5) {
+        double v5[5];
 #pragma unroll
-        for (int k = 5; k < kStats; ++k) partials[(size_t)kStats * blockIdx.x + k] = tail[k - 5];
+        for (int k = 0; k < 5; ++k) v5[k] = base + k < kStats ? acc[base + k] : 0.0;
+        block_sum5(v5, tail);
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 5 && base + k < kStats; ++k) partials[(size_t)kStats * blockIdx.x + base + k] = tail[k];
+        __syncthreads();
     }
 }
 

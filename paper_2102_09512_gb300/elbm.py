@@ -183,7 +183,7 @@ def elbm_step_totals(h) -> np.ndarray:
 
 
 STATS_KEYS = ("rho_mean", "rho_rms", "K", "u_rms", "theta_rms", "T_mean", "T_rms", "dudx2", "omega_rms",
-              "enstrophy")
+              "enstrophy", "dissipation", "lambda", "Re_lambda")
 
 
 def elbm_turbulence_stats(h) -> dict:

@@ -1,5 +1,6 @@
-"""Post-processing probes of the shock-vortex interaction (paper Sec. III.C) on
-fields extracted from a solver (host numpy arrays, lattice units).
+"""Post-processing probes on fields extracted from a solver (lattice units): the
+shock-vortex interaction (paper Sec. III.C) and the energy spectrum of decaying
+turbulence (Sec. III.D).
 
 The sound pressure is Delta P = (P - P_s) / P_s with P = rho T (R = 1) and P_s the
 pressure behind the shock; it is read along a ray from the vortex centre at an angle
@@ -58,3 +59,51 @@ def radial_sound_pressure(rho: np.ndarray, T: np.ndarray, centre, theta_deg: flo
     x = centre[0] + np.asarray(r) * math.cos(th)
     y = centre[1] + np.asarray(r) * math.sin(th)
     return (bilinear(rho * T, x, y) - P_s) / P_s
+
+
+def energy_spectrum(u) -> tuple:
+    """Shell-summed kinetic energy spectrum E(k) of a periodic (3, n, n, n) velocity
+    field (numpy or torch; torch tensors are transformed on their device):
+    E(k) = sum over integer shells |k| in [k - 1/2, k + 1/2) of |u_hat|^2 / 2, with
+    u_hat the FFT normalised by n^3, so that sum_k E(k) = <u.u>/2.  Returns (k, E)
+    as numpy arrays over every shell, k = 0 .. round(sqrt(3) n/2) (shells above n/2 are
+    only partly inside the transform's cube)."""
+    n = u.shape[-1]
+    nk = int(round(math.sqrt(3.0) * (n // 2))) + 1
+    try:
+        import torch
+        is_torch = isinstance(u, torch.Tensor)
+    except ImportError:
+        is_torch = False
+    kk = np.fft.fftfreq(n, d=1.0 / n)
+    kr = np.fft.rfftfreq(n, d=1.0 / n)
+    if is_torch:
+        dev = u.device
+        kz = torch.as_tensor(kk, device=dev).view(n, 1, 1)
+        ky = torch.as_tensor(kk, device=dev).view(1, n, 1)
+        kx = torch.as_tensor(kr, device=dev).view(1, 1, -1)
+        shell = torch.round(torch.sqrt(kx * kx + ky * ky + kz * kz)).long()
+        # the half-spectrum counts every k_x > 0 (except the Nyquist plane) twice
+        wgt = torch.full((1, 1, kr.size), 2.0, device=dev, dtype=torch.float64)
+        wgt[..., 0] = 1.0
+        if n % 2 == 0:
+            wgt[..., -1] = 1.0
+        E = torch.zeros(nk, dtype=torch.float64, device=dev)
+        for a in range(3):
+            uh = torch.fft.rfftn(u[a].to(torch.float64), dim=(0, 1, 2)) / float(n) ** 3
+            e = 0.5 * (uh.real ** 2 + uh.imag ** 2) * wgt
+            E.index_add_(0, shell.reshape(-1), e.reshape(-1))
+            del uh, e
+        E = E.cpu().numpy()
+    else:
+        kz, ky, kx = np.meshgrid(kk, kk, kr, indexing="ij")
+        shell = np.rint(np.sqrt(kx * kx + ky * ky + kz * kz)).astype(np.int64)
+        wgt = np.full(kr.size, 2.0)
+        wgt[0] = 1.0
+        if n % 2 == 0:
+            wgt[-1] = 1.0
+        E = np.zeros(nk)
+        for a in range(3):
+            uh = np.fft.rfftn(np.asarray(u[a], dtype=np.float64)) / float(n) ** 3
+            np.add.at(E, shell.ravel(), (0.5 * np.abs(uh) ** 2 * wgt).ravel())
+    return np.arange(nk), E

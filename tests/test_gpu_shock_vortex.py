@@ -15,7 +15,6 @@ import numpy as np
 import pytest
 
 from paper_2102_09512_gb300 import cases as C
-from paper_2102_09512_gb300 import probes as PR
 
 pytestmark = pytest.mark.gpu
 
@@ -32,26 +31,11 @@ def E():
 
 @pytest.fixture(scope="module")
 def run(E):
-    c = C.shock_vortex(1680, 1440, r_v=60.0, Ma_s=1.2, Ma_v=0.25, inflow=True)
-    nx, ny = c.nx, c.ny
-    rv, cs, P_s, u_s, u_l = c.extra["r_v"], c.extra["cs_l"], c.extra["P_s"], c.extra["u_s"], c.fixed[1]
-    xv, yv, xs = c.extra["x_v"], c.extra["y_v"], c.extra["x_s"]
-    t_hit = (xs - xv) / u_l
-    g = E.Solver.from_case(c, store="f64")
-    out, t = {}, 0
-    r = np.arange(0.0, 8.0 * rv + 0.5, 1.0)
-    for ts in (6, 8):
-        steps = int(round(ts * rv / cs))
-        g.step(steps - t)
-        t = steps
-        rho, u, T = g.fields()
-        rho, T, u = rho.reshape(ny, nx), T.reshape(ny, nx), u.reshape(2, ny, nx)
-        pred = (xs + u_s * (t - t_hit), yv)
-        centre = PR.vortex_centre(u, pred, int(1.5 * rv))
-        out[ts] = dict(pred=pred, centre=centre, r=r / rv,
-                       dp=PR.radial_sound_pressure(rho, T, centre, -45.0, r, P_s))
-    g.close()
-    return c, out
+    from paper_2102_09512_gb300 import studies
+    out = studies.shock_vortex_sound(times=(6.0, 8.0), store="f64")
+    res = {int(ts): dict(pred=e["predicted"], centre=e["centre"], r=e["r_over_rv"], dp=e["delta_p"])
+           for ts, e in out["results"].items()}
+    return out["case"], res
 
 
 def test_vortex_track(run):

@@ -30,9 +30,14 @@ def host_stats(c, rho, u, T):
     # vorticity: axes of the arrays are (z, y, x)
     w2 = ((d(U[2], 1) - d(U[1], 0)) ** 2 + (d(U[0], 0) - d(U[2], 2)) ** 2 + (d(U[1], 2) - d(U[0], 1)) ** 2)
     uu = (U ** 2).sum(0)
-    return dict(rho_mean=r.mean(), rho_rms=r.std(), K=0.5 * (r * uu).mean(), u_rms=np.sqrt(uu.mean() / 3),
+    mu = c.mu0 * (Tt / c.T0) ** c.mu_exp
+    dudx2 = (d(U[0], 2) ** 2).mean()
+    lam = np.sqrt((U[0] ** 2).mean() / dudx2)
+    u_rms = np.sqrt(uu.mean() / 3)
+    return dict(rho_mean=r.mean(), rho_rms=r.std(), K=0.5 * (r * uu).mean(), u_rms=u_rms,
                 theta_rms=np.sqrt((theta ** 2).mean()), T_mean=Tt.mean(), T_rms=Tt.std(),
-                dudx2=(d(U[0], 2) ** 2).mean(), omega_rms=np.sqrt(w2.mean()), enstrophy=0.5 * w2.mean())
+                dudx2=dudx2, omega_rms=np.sqrt(w2.mean()), enstrophy=0.5 * w2.mean(),
+                dissipation=(mu * w2).mean(), **{"lambda": lam}, Re_lambda=r.mean() * u_rms * lam / c.mu0)
 
 
 def test_device_statistics_match_host(E):
@@ -109,3 +114,34 @@ def test_enstrophy_grid_study(E):
         k_end.append(K[-1])
     assert peaks[0] < peaks[1] < peaks[2] and peaks[2] > 1.4
     assert abs(k_end[2] - k_end[1]) < abs(k_end[1] - k_end[0])
+
+
+def test_initial_taylor_reynolds_number(E):
+    """The device statistics of the initial state return the generator's Re_lambda
+    (Eq. Taylor_Re with lambda = sqrt(<u_x^2>/<(d_x u_x)^2>)) and a Kolmogorov-type
+    spectrum peak near kappa_0."""
+    from paper_2102_09512_gb300 import probes as PR
+    c = C.hit(64, k0=4.0, Ma_t=0.488, Re_lambda=175.0)
+    g = E.Solver.from_case(c, store="f64")
+    s = g.turbulence_stats()
+    assert s["Re_lambda"] == pytest.approx(175.0, rel=1e-9)
+    assert s["lambda"] == pytest.approx(c.extra["lambda_"], rel=1e-9)
+    _, u, _ = g.fields()
+    k, Ek = PR.energy_spectrum(u.reshape(3, 64, 64, 64))
+    assert 3 <= int(np.argmax(Ek)) <= 5
+    assert Ek.sum() == pytest.approx(0.5 * (u ** 2).sum(0).mean(), rel=1e-10)
+    g.close()
+
+
+def test_decaying_turbulence_study_driver(E):
+    """The Sec. III.D driver at 64^3 to t* = 1: statistics every tau/4, spectra at t* = 0
+    and 1, kinetic energy decaying and Re_lambda starting at the requested value."""
+    from paper_2102_09512_gb300 import studies
+    out = studies.decaying_turbulence(n=64, Ma_t=0.3, Re_lambda=72.0, k0=4.0, t_end=1.0, spectra_at=(0.0, 1.0))
+    h = out["hist"]
+    assert len(h) == 5 and abs(h[-1]["t_star"] - 1.0) < 0.13
+    assert h[0]["Re_lambda"] == pytest.approx(72.0, rel=1e-6)
+    assert h[-1]["K"] < h[0]["K"]
+    assert set(out["spectra"]) == {0.0, 1.0}
+    k, Ek = out["spectra"][1.0]
+    assert Ek.sum() == pytest.approx(h[-1]["u_rms"] ** 2 * 1.5, rel=1e-6)

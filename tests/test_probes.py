@@ -3,6 +3,7 @@ centre and radial sound pressure on synthetic fields with known answers."""
 import math
 
 import numpy as np
+import pytest
 
 from paper_2102_09512_gb300 import cases as C
 from paper_2102_09512_gb300 import probes as PR
@@ -45,3 +46,29 @@ def test_radial_sound_pressure_along_the_ray():
     hit = PR.radial_sound_pressure(marker + 1.0, np.ones_like(rr), (50.0, 50.0), -45.0,
                                    np.array([7.0 * math.sqrt(2.0)]), 1.0)
     assert hit[0] == 1.0
+
+
+def test_energy_spectrum_of_single_modes():
+    """A Fourier mode of wavenumber (3, 4, 0) (|k| = 5) puts all its energy <u.u>/2 in
+    shell 5; a uniform flow puts its energy in shell 0; the sum is <u.u>/2."""
+    n = 16
+    z, y, x = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    u = np.zeros((3, n, n, n))
+    u[2] = 0.3 * np.cos(2 * np.pi * (3 * x + 4 * y) / n + 0.7)
+    u[0] = 0.1
+    k, E = PR.energy_spectrum(u)
+    assert k[5] == 5
+    assert E[5] == pytest.approx(0.5 * np.mean(u[2] ** 2), rel=1e-12)
+    assert E[0] == pytest.approx(0.5 * 0.01, rel=1e-12)
+    assert E.sum() == pytest.approx(0.5 * np.mean((u ** 2).sum(0)), rel=1e-12)
+
+
+def test_energy_spectrum_torch_matches_numpy():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(2)
+    u = rng.standard_normal((3, 12, 12, 12))
+    k1, E1 = PR.energy_spectrum(u)
+    k2, E2 = PR.energy_spectrum(torch.as_tensor(u))
+    assert np.array_equal(k1, k2)
+    assert np.allclose(E1, E2, rtol=1e-12, atol=1e-15)
+    assert E1.sum() == pytest.approx(0.5 * np.mean((u ** 2).sum(0)), rel=1e-12)
