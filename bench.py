@@ -38,6 +38,9 @@ BYTES_PER_UPDATE = {"f64": 864, "f32": 432, "f16dev": 216, "bf16dev": 216}
 METRIC = "D3Q27 two-pop GLUPS at 256^3: FP16-store vs FP32 vs FP64; % of HBM roofline"
 WORKLOAD = "D3Q27 decaying compressible turbulence 256^3, periodic, Ma_t=0.5, Re_lambda=72"
 FALLBACK_HBM_GBS = 6800.0
+# step schedules (elbm_kernel): one fused kernel, two passes, fused with the plane
+# gathered twice, fused with bulk-copy (TMA) plane staging
+KERNELS = {"fused": 0, "twopass": 1, "reread": 2, "bulk": 3}
 
 
 def _dist():
@@ -219,9 +222,10 @@ def run_reference(args):
     return 0
 
 
-def time_store(E, torch, case, store, steps, warmup, stream):
+def time_store(E, torch, case, store, steps, warmup, stream, kernel=0):
     """Device-resident timing of `steps` steps; returns (ms_per_step, launches, solver)."""
     g = E.Solver.from_case(case, store=store, stream=stream)
+    g.set_kernel(kernel)
     for w in range(warmup):
         g.step(1)
         rc = E.elbm_sync(g.h)
@@ -317,6 +321,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--size", type=int, default=N_SIDE, help="box side (the bench workload is 256)")
+    ap.add_argument("--kernel", default="fused", choices=sorted(KERNELS),
+                    help="step schedule of the timed stores (default: the library's fused kernel)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -358,7 +364,7 @@ def main():
         if sampler:
             sampler.start()
         try:
-            ms, launches, g = time_store(E, torch, case, store, k, args.warmup, stream)
+            ms, launches, g = time_store(E, torch, case, store, k, args.warmup, stream, KERNELS[args.kernel])
         except E.ElbmError as err:
             if sampler:
                 sampler.stop()
@@ -409,7 +415,7 @@ def main():
         v, cores, sample = cpu_oracle_sample()
         cpu = {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle", "sample": sample}
 
-    kernel_key = f"fused3d_{head}_{n_side}"
+    kernel_key = f"fused3d_{head}_{n_side}" if args.kernel == "fused" else f"{args.kernel}_{head}_{n_side}"
     traffic = _ncu_traffic(kernel_key)
     roofline = {"bound": "hbm", "achieved": hs["algorithmic_GBs_per_gpu"], "peak": peak, "unit": "GB/s",
                 "frac": hs["algorithmic_GBs_per_gpu"] / peak, "peak_kind": peak_kind,
@@ -421,7 +427,7 @@ def main():
         "vs_baseline": None, "dtype": "f32" if head != "f64" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if n_side == N_SIDE else WORKLOAD.replace("256^3", f"{n_side}^3"),
                    "lattice": "D3Q27", "grid": [n_side] * 3, "store": head,
-                   "schedule": "fused", "l2": "inputs larger than L2 (3.6 GB FP32 store)",
+                   "schedule": args.kernel, "l2": "inputs larger than L2 (3.6 GB FP32 store)",
                    "parallelism": "replicas" if ws > 1 else "single-gpu"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_head,
         "clocks": clocks, "variants": variants, "ensemble": ens,

@@ -83,8 +83,17 @@ typedef enum {
                                      D3Q27 FP32/FP16/BF16 prefetch each plane into shared
                                      memory (cp.async), FP64 uses the re-read form */
     ELBM_KERNEL_TWOPASS = 1,      /* moment/Q~ pass into the aux buffer, then collide+stream */
-    ELBM_KERNEL_FUSED_REREAD = 2  /* one kernel, D3Q27 plane gathered twice (second from L2);
+    ELBM_KERNEL_FUSED_REREAD = 2, /* one kernel, D3Q27 plane gathered twice (second from L2);
                                      D2Q9 runs the fused kernel */
+    ELBM_KERNEL_FUSED_BULK = 3    /* one kernel, D3Q27 FP32/FP16/BF16: the rows of each plane
+                                     are copied into shared memory by the bulk asynchronous
+                                     copy engine (TMA), completion counted on an mbarrier.
+                                     Needs a periodic x axis with nx a multiple of 2 (FP32)
+                                     or 4 (FP16/BF16) and nx >= 36 (FP32) or 40; otherwise
+                                     elbm_set_kernel returns ELBM_ERR_UNSUPPORTED.  Its
+                                     waits are bounded (about 1 s): one that gives up is
+                                     reported as ELBM_ERR_TIMEOUT by the next
+                                     synchronising call */
 } elbm_kernel;
 
 typedef struct {

@@ -107,7 +107,7 @@ int sync_status(elbm_handle* h) {
         e = cudaMemsetAsync(status_ptr(h), 0, sizeof(int), h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return ELBM_ERR_CUDA;
-        return ELBM_ERR_NONPHYSICAL;
+        return (st & kStatusTimeoutBit) ? ELBM_ERR_TIMEOUT : ELBM_ERR_NONPHYSICAL;
     }
     return ELBM_OK;
 }
@@ -231,6 +231,9 @@ int elbm_step(elbm_handle* h, int nsteps) {
         else if (h->kernel == ELBM_KERNEL_FUSED_REREAD)
             e = h->ops->step_fused_reread(h->kp, src, dst, step_partials(h), &h->step_blocks, status_ptr(h),
                                           h->stream, &h->launches);
+        else if (h->kernel == ELBM_KERNEL_FUSED_BULK)
+            e = h->ops->step_fused_bulk(h->kp, src, dst, step_partials(h), &h->step_blocks, status_ptr(h),
+                                        h->stream, &h->launches);
         else
             e = h->ops->step_fused(h->kp, src, dst, step_partials(h), &h->step_blocks, status_ptr(h), h->stream,
                                    &h->launches);
@@ -305,8 +308,10 @@ int elbm_step_totals(elbm_handle* h, double out[5]) {
 }
 
 int elbm_set_kernel(elbm_handle* h, int kernel) {
-    if (!h || (kernel != ELBM_KERNEL_FUSED && kernel != ELBM_KERNEL_TWOPASS && kernel != ELBM_KERNEL_FUSED_REREAD))
+    if (!h || (kernel != ELBM_KERNEL_FUSED && kernel != ELBM_KERNEL_TWOPASS && kernel != ELBM_KERNEL_FUSED_REREAD &&
+               kernel != ELBM_KERNEL_FUSED_BULK))
         return ELBM_ERR_ARG;
+    if (kernel == ELBM_KERNEL_FUSED_BULK && !h->ops->bulk_supported(h->kp)) return ELBM_ERR_UNSUPPORTED;
     h->kernel = kernel;
     return ELBM_OK;
 }

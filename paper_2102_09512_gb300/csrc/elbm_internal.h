@@ -182,6 +182,11 @@ struct AuxLayout {
 
 // Device-side description of a D2Q9 ensemble (arrays live in the ensemble's
 // auxiliary buffer).
+// Bits of the device status word: a non-physical state (rho <= 0, T <= 0 or not
+// finite) and a bounded device wait that gave up.
+constexpr int kStatusNonphysicalBit = 1;
+constexpr int kStatusTimeoutBit = 2;
+
 constexpr int kMaxEnsemble = 1024;
 struct EnsembleArgs {
     const KParams* params;      // [n] per-instance parameters
@@ -223,6 +228,9 @@ struct Ops {
                          long long* launches);   // kStatsSums partial sums per CTA
     int fused_tile_y;             // tile height of the fused kernels (tile width 32)
     int (*fused_occupancy)();     // resident CTAs per SM of the default fused D3Q27 kernel (0: unknown)
+    cudaError_t (*step_fused_bulk)(const KParams& p, const void* src, void* dst, double* partials,
+                                   int* nblocks, int* status, cudaStream_t s, long long* launches);
+    int (*bulk_supported)(const KParams& p);   // the grid suits the bulk-staged D3Q27 kernel
 };
 
 // z-segment length of the fused D3Q27 kernels.  Each CTA marches one (tile, segment)

@@ -801,6 +801,274 @@ fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPla
     block_sum5(tot, partials + 5 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
 }
 
+// ---------------------------------------------------------------------------
+// D3Q27 with bulk-copy plane staging
+// ---------------------------------------------------------------------------
+// The bulk asynchronous copy engine (cp.async.bulk, the TMA unit) moves whole rows of
+// a direction plane from global to shared memory; the copies of one plane count
+// their bytes on an mbarrier, which the consuming threads wait on.
+__device__ __forceinline__ unsigned smem_u32(const void* ptr) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(ptr));
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// One arrival that also announces `bytes` of copies for the current phase.
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+// Waits for the phase of parity `parity` to complete, for at most about one second;
+// false if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try(bar, parity))
+        if (global_ns() - t0 > 1000000000ull) return false;
+    return true;
+}
+// Orders this thread's earlier shared-memory accesses before later async-proxy writes.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) into shared
+// memory, completing on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Shared-memory plan of the bulk-staged kernel.  For every direction i the buffer of
+// plane q holds a box of RB rows x BW columns of the SOURCE plane q - c_z: rows
+// y0 - 1 - c_y ... y0 + TY - c_y and columns x0 - XO ... x0 + TX + XO - 1, so that node
+// (x, y) of the tile and its halo ring finds its pulled pair of direction i at box row
+// y - y0 + 1 and column x - x0 + XO - c_x.  XO keeps every row copy 16-byte aligned.
+template <int TY>
+struct Bulk {
+    static constexpr int XO = 16 / (int)sizeof(P);
+    static constexpr int BW = TX + 2 * XO;
+    static constexpr int RB = TY + 2;
+    static constexpr int BOX = RB * BW;
+    static constexpr unsigned plane_bytes = (unsigned)(Q * BOX * sizeof(P));
+    static constexpr size_t buf_bytes = (size_t)2 * plane_bytes;
+    static constexpr size_t q_bytes = (size_t)2 * (TY * (TX + 2) + (TY + 2) * TX) * sizeof(R);
+    static constexpr size_t smem_bytes = buf_bytes + q_bytes + 2 * sizeof(unsigned long long);
+    static constexpr int NTASK = Q * RB;   // row copies per plane
+};
+
+// D3Q27, pipelined on bulk copies.  The same march as fused3d_kernel (a TX x TY column
+// over a z segment, two plane buffers, plane z+2 requested while plane z+1's moments
+// and plane z's collision run), but the pulled pairs arrive as row copies issued by
+// threads NH.. (about one copy per thread per plane instead of 27 per-pair copies),
+// and a plane's completion is one mbarrier phase.  Per plane z:
+//   wait for plane z+1's phase; read the pairs of plane z into registers; barrier
+//   (every thread has read plane z's buffer; the Q~ arrays are free); request plane
+//   z+2 into plane z's buffer; moments of plane z+1 (tile and halo) -> Q~; collide
+//   plane z and store.
+// A wait that gives up (about one second) latches kStatusTimeoutBit, and the CTA stops
+// after waiting, again bounded, for the copies it still has in flight.
+// It is a selectable schedule, not the default: a plane is about 300 row copies of
+// 160-288 bytes, and their per-copy cost in the copy engine, not the bytes, sets the
+// pace (at 256^3 it reaches about 3/4 of fused3d_kernel's rate; with one warp issuing
+// all copies instead of six, a third of it).  Each copy is one bulk operation because
+// the pulled window of a direction is a box of short rows; one copy per box would need
+// a tensor map and a separate path for the tiles whose box wraps around the grid.
+template <int TY, int MINB, int DD, bool CAL>
+__global__ void __launch_bounds__(TX * TY, MINB)
+fused3d_bulk_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPlanes pl,
+                    const P* __restrict__ src, double* __restrict__ partials, int* __restrict__ status) {
+    using BB = Bulk<TY>;
+    static_assert(sizeof(R) == 4 && DD == 3, "the bulk-staged kernel is D3Q27 in FP32 arithmetic");
+    constexpr int NT = TX * TY, NH = 2 * TX + 2 * TY, XO = BB::XO, BW = BB::BW, RB = BB::RB, BOX = BB::BOX;
+    static_assert(NT > NH, "row copies are issued by the threads without a halo node");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    P* buf = reinterpret_cast<P*>(smem_raw);                                // [2][Q][RB][BW]
+    R* qxs = reinterpret_cast<R*>(smem_raw + BB::buf_bytes);                // [2][TY][TX+2]
+    R* qys = qxs + 2 * TY * (TX + 2);                                       // [2][TY+2][TX]
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + BB::buf_bytes + BB::q_bytes);
+    auto QX = [&](int b, int row, int col) -> R& { return qxs[(b * TY + row) * (TX + 2) + col]; };
+    auto QY = [&](int b, int row, int col) -> R& { return qys[(b * (TY + 2) + row) * TX + col]; };
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int zb = blockIdx.z * p.tz, ze = min(zb + p.tz, p.nz);
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < p.nx && y < p.ny;
+    const int xl = min(x0 + TX, p.nx) - 1 - x0, yl = min(y0 + TY, p.ny) - 1 - y0;
+    const int nslot = (ty + 1) * BW + tx + XO;   // this node in a direction's box (before -c_x)
+
+    // this thread's halo node: its box position is the unmapped one on a periodic axis
+    // and the mapped (clamped) node's on a zero-gradient axis
+    int hx = 0, hy = 0, hsx = 0, hsy = 0, haxis = 0, hslot = 0;
+    const bool has_halo = tid < NH && halo_node<TY>(p, tid, x0, y0, xl, yl, hx, hy, hsx, hsy, haxis);
+    if (has_halo) {
+        const int ux = haxis == 1 ? x0 + hsx : x0 + hsx - 1;
+        const int uy = haxis == 1 ? y0 + hsy - 1 : y0 + hsy;
+        hslot = ((p.per_y ? uy : hy) - y0 + 1) * BW + (ux - x0 + XO);
+    }
+
+    // row copies of source plane q - c_z for every direction into buffer sb; thread 0
+    // announces the plane's bytes (a phase completes when they have all landed)
+    unsigned issued = 0u;   // planes requested per buffer: buffer 0 in the low half, 1 in the high
+    auto issue_plane = [&](int q, int sb) {
+        const unsigned bar = smem_u32(&bars[sb]);
+        issued += sb ? 0x10000u : 1u;
+        if (tid == 0) mbar_expect_tx(bar, BB::plane_bytes);
+        if (tid >= NH) {
+            fence_proxy_async();
+            for (int t = tid - NH; t < BB::NTASK; t += NT - NH) {
+                const int i = t / RB, r = t - RB * i;
+                const int b = (i / 3) % 3, c = i / 9;
+                int ys = y0 + r - b;   // y0 - 1 - c_y + r
+                if (p.per_y) {   // ys is in [y0 - 2, y0 + TY + 1]: a few periods at most
+                    while (ys < 0) ys += p.ny;
+                    while (ys >= p.ny) ys -= p.ny;
+                } else {
+                    ys = min(max(ys, 0), p.ny - 1);
+                }
+                const int zs = map_axis(q + 1 - c, p.nz, p.per_z);   // q - c_z
+                const P* row = pl.src[i] + (unsigned)(p.nx * (ys + p.ny * zs));
+                const unsigned d = smem_u32(buf + ((size_t)sb * Q + i) * BOX + r * BW);
+                const int xs = x0 - XO;
+                if (xs < 0) {   // columns -XO .. -1 are the last XO of the row
+                    bulk_g2s(d, row + (p.nx - XO), XO * sizeof(P), bar);
+                    bulk_g2s(d + XO * sizeof(P), row, (BW - XO) * sizeof(P), bar);
+                } else if (xs + BW > p.nx) {   // columns nx .. wrap to 0 ..
+                    const int n1 = p.nx - xs;
+                    bulk_g2s(d, row + xs, n1 * sizeof(P), bar);
+                    bulk_g2s(d + n1 * sizeof(P), row, (BW - n1) * sizeof(P), bar);
+                } else {
+                    bulk_g2s(d, row + xs, BW * sizeof(P), bar);
+                }
+            }
+        }
+    };
+    auto slot_moments = [&](int sb, int slot, Moments<R>& m, auto full) {
+        const P* bb = buf + (size_t)sb * Q * BOX + slot;
+        R f[Q], g[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Cd::dec(bb[i * BOX - cx_of(i)], f[i], g[i]);
+        node_moments<kD, R, decltype(full)::value, DEV, CAL>(f, g, p, m);
+    };
+    using Full = std::true_type;
+    using Lite = std::false_type;
+
+    if (tid == 0) {
+        mbar_init(smem_u32(&bars[0]), 1);
+        mbar_init(smem_u32(&bars[1]), 1);
+    }
+    __syncthreads();
+
+    Acc5 acc;
+    acc.zero();
+    bool bad = false, late = false;
+
+    // prologue: Q~_zzz below the segment, planes zb and zb+1 in flight, moments of zb
+    R qz_prev = R(0), qz_cur = R(0), qz_next = R(0);
+    if (active) qz_prev = direct_anomaly_z<CAL>(p, src, x, y, map_axis(zb - 1, p.nz, p.per_z));
+    issue_plane(zb, 0);
+    issue_plane(map_axis(zb + 1, p.nz, p.per_z), 1);
+    Moments<R> m_cur, m_next;
+    late |= !mbar_wait(smem_u32(&bars[0]), 0);
+    if (active) {
+        slot_moments(0, nslot, m_cur, Full());
+        QX(0, ty, tx + 1) = anomaly(m_cur.rho, m_cur.ux, m_cur.T);
+        QY(0, ty + 1, tx) = anomaly(m_cur.rho, m_cur.uy, m_cur.T);
+        qz_cur = anomaly(m_cur.rho, m_cur.uz, m_cur.T);
+    }
+    if (has_halo) {
+        Moments<R> hm;
+        slot_moments(0, hslot, hm, Lite());
+        if (haxis == 1) QY(0, hsy, hsx) = anomaly(hm.rho, hm.uy, hm.T);
+        else QX(0, hsy, hsx) = anomaly(hm.rho, hm.ux, hm.T);
+    }
+
+    bool gave_up = false;
+    for (int z = zb; z < ze; ++z) {
+        const int k = z - zb;
+        const int sz = k & 1, sn = sz ^ 1;   // buffers (and Q~ arrays) of planes z and z+1
+        const bool last = (z + 1 == ze);
+        late |= !mbar_wait(smem_u32(&bars[sn]), ((k + 1) >> 1) & 1);
+        P pk[Q];   // the pulled pairs of plane z, as stored
+        if (active) {
+            const P* bb = buf + (size_t)sz * Q * BOX + nslot;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) pk[i] = bb[i * BOX - cx_of(i)];
+        }
+        if (__syncthreads_or(late)) {
+            gave_up = true;
+            break;
+        }
+        if (z + 2 <= ze) issue_plane(map_axis(z + 2, p.nz, p.per_z), sz);
+
+        if (active) {
+            slot_moments(sn, nslot, m_next, Full());
+            qz_next = anomaly(m_next.rho, m_next.uz, m_next.T);
+            if (!last) {
+                QX(sn, ty, tx + 1) = anomaly(m_next.rho, m_next.ux, m_next.T);
+                QY(sn, ty + 1, tx) = anomaly(m_next.rho, m_next.uy, m_next.T);
+            }
+        }
+        if (!last && has_halo) {
+            Moments<R> hm;
+            slot_moments(sn, hslot, hm, Lite());
+            if (haxis == 1) QY(sn, hsy, hsx) = anomaly(hm.rho, hm.uy, hm.T);
+            else QX(sn, hsy, hsx) = anomaly(hm.rho, hm.ux, hm.T);
+        }
+        if (active) {
+            bad |= nonphysical(m_cur);
+            const R Dx = dQ(p.deriv, m_cur.ux, QX(sz, ty, tx), QX(sz, ty, tx + 1), QX(sz, ty, tx + 2));
+            const R Dy = dQ(p.deriv, m_cur.uy, QY(sz, ty, tx), QY(sz, ty + 1, tx), QY(sz, ty + 2, tx));
+            const R Dz = dQ(p.deriv, m_cur.uz, qz_prev, qz_cur, qz_next);
+            R v[5];
+            node_totals(m_cur, m_cur.rE, v);
+            acc.add(v);
+            Relax<kD, R, DEV, CAL> rx;
+            rx.init(m_cur, Dx, Dy, Dz, p);
+            const unsigned n = (unsigned)node_index(p, x, y, z);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                R f, g;
+                Cd::dec(pk[i], f, g);
+                pl.dst[i][n] = Cd::enc(rx.f(i, f, p), rx.g(i, g, p));
+            }
+        }
+        m_cur = m_next;
+        qz_prev = qz_cur;
+        qz_cur = qz_next;
+    }
+    if (gave_up) {
+        // the last phase of each buffer may still have copies in flight
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const unsigned n = b ? issued >> 16 : issued & 0xffffu;
+            if (n) mbar_wait(smem_u32(&bars[b]), (n - 1) & 1);
+        }
+        if (tid == 0) atomicOr(status, kStatusTimeoutBit);
+    }
+    flag_if(bad, status);
+    double tot[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) tot[k] = (double)acc.s[k] - (double)acc.c[k];
+    block_sum5(tot, partials + 5 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
+}
+
 // D3Q27 without plane buffers: for plane z it computes Q~ of plane z+1 (tile + halo)
 // from a first gather, then gathers plane z again (an L2 hit) to collide it.
 template <int TY, bool CAL>
@@ -916,6 +1184,18 @@ using PipeCfg = Pipe<kTY3, kNB>;
 #define ELBM_EARLY 1
 #endif
 constexpr bool kEarly = ELBM_EARLY && kMinB == 1;
+// Bulk-staged D3Q27 kernel: FP32 plane buffers (152 KB) leave room for one CTA per SM,
+// FP16/BF16 ones (84 KB) for two.
+using BulkCfg = Bulk<kTY3>;
+constexpr int kBulkMinB = (BulkCfg::smem_bytes * 2 + 4096 <= 228 * 1024) ? 2 : 1;
+
+// Can the bulk-staged kernel run this grid?  x must be periodic (a row that leaves the
+// grid wraps around as a second copy), nx a multiple of XO (rows stay 16-byte aligned)
+// and at least one box wide (a row wraps at most once).
+int bulk_supported(const KParams& p) {
+    if (kD != 3 || !kPipe) return 0;
+    return p.per_x && p.nx % BulkCfg::XO == 0 && p.nx >= BulkCfg::BW && !p.has_fixed;
+}
 
 inline unsigned blocks_1d(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
@@ -999,6 +1279,38 @@ cudaError_t launch_fused_cal(const KParams& p, const void* src, void* dst, doubl
                                                                               status);
     }
     return cudaGetLastError();
+}
+
+template <int DD, bool CAL>
+cudaError_t launch_bulk_cal(const KParams& p, const void* src, void* dst, double* partials, int* status,
+                            cudaStream_t s) {
+    if constexpr (DD == 3 && kPipe) {
+        auto kern = fused3d_bulk_kernel<kTY3, kBulkMinB, DD, CAL>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)BulkCfg::smem_bytes);
+        if (e != cudaSuccess) return e;
+        DirPlanes pl;
+        for (int i = 0; i < Q; ++i) {
+            pl.src[i] = (const P*)src + (size_t)i * (size_t)p.N;
+            pl.dst[i] = (P*)dst + (size_t)i * (size_t)p.N;
+        }
+        kern<<<fused_grid(p), dim3(TX, kTY3), BulkCfg::smem_bytes, s>>>(p, pl, (const P*)src, partials, status);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+// Bulk-staged fused step (callers check bulk_supported first).
+cudaError_t launch_fused_bulk(const KParams& p, const void* src, void* dst, double* partials, int* nblocks,
+                              int* status, cudaStream_t s, long long* launches) {
+    if (!bulk_supported(p)) return cudaErrorInvalidValue;
+    const cudaError_t e = p.eos ? launch_bulk_cal<kD, true>(p, src, dst, partials, status, s)
+                                : launch_bulk_cal<kD, false>(p, src, dst, partials, status, s);
+    ++*launches;
+    const dim3 grid = fused_grid(p);
+    *nblocks = (int)(grid.x * grid.y * grid.z);
+    return e;
 }
 
 template <int DD>
@@ -1098,7 +1410,7 @@ int fused_occupancy() { return fused_occupancy_impl<kD>(); }
 const Ops kOps = {kD,          kST,           sizeof(P) / 2,  sizeof(R),            max_blocks,
                   launch_init, launch_fields, launch_twopass, launch_fused_default, launch_fused_reread,
                   launch_totals, launch_ensemble, ensemble_occupancy, launch_stats,
-                  kD == 3 ? kTY3 : kTY2, fused_occupancy};
+                  kD == 3 ? kTY3 : kTY2, fused_occupancy, launch_fused_bulk, bulk_supported};
 
 }  // namespace
 
