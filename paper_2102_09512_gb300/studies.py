@@ -8,6 +8,9 @@ statistics (elbm_turbulence_stats) and the host probes (probes.py).
                         spectra (on the device with torch.fft).
   shock_vortex_sound    Sec. III.C: vortex track and radial sound pressure Delta P
                         along theta from the vortex centre at t* = t c_s,l / r_v.
+  precision_study       reduced-precision population stores (FP32, FP16 and BF16
+                        deviations) against a GPU FP64 run of the same decaying-turbulence
+                        field: relative L2 errors of rho, u, T and statistics drift.
 """
 from __future__ import annotations
 
@@ -102,3 +105,92 @@ def shock_vortex_sound(nx: int = 1680, ny: int = 1440, r_v: float = 60.0, Ma_s: 
     finally:
         g.close()
     return dict(case=c.extra, results=out)
+
+
+def _rel_l2(a, b) -> float:
+    import torch
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def precision_study(n: int = 256, steps: int = 100, stores=("f32", "f16dev", "bf16dev"), every: int = 10,
+                    survive: int = 0, seed: int = 20210218, k0: float = 4.0, Ma_t: float = 0.5,
+                    Re_lambda: float = 72.0) -> dict:
+    """The decaying-turbulence field of Sec. III.D on an n^3 periodic D3Q27 box (the
+    bench workload at n = 256) run with the FP64 store and with each store in
+    `stores`.  For every store, after `steps` steps: the relative L2 error of rho, u
+    (all components) and T against the FP64 run, the same for the fluctuations
+    rho - <rho> and T - <T> (the plain metric is lenient because of the means), and the
+    K(t) and theta_rms(t) histories (sampled every `every` steps) with their relative
+    deviation from FP64's; the largest deviation is taken over t > 0 (the initial
+    dilatation is near zero, so its relative deviation says nothing).  Every run then
+    continues to `survive` steps (if larger) and reports the last sample at which its
+    state was still physical.  Errors are computed on the device."""
+    import torch
+
+    c = C.hit(n, seed=seed, k0=k0, Ma_t=Ma_t, Re_lambda=Re_lambda, dtype=np.float32 if n > 256 else np.float64)
+    N = n ** 3
+    dev = torch.device("cuda")
+    t_end = max(steps, survive)
+
+    def run(store):
+        g = E.Solver.from_case(c, store=store)
+        hist, t, wall, fields, last_ok = [], 0, 0.0, None, 0
+        try:
+            while True:
+                s = g.turbulence_stats()   # synchronises; raises if the state is non-physical
+                last_ok = t
+                hist.append((t, s["K"], s["theta_rms"]))
+                if t == steps:
+                    rho = torch.empty(N, dtype=torch.float64, device=dev)
+                    u = torch.empty(3 * N, dtype=torch.float64, device=dev)
+                    T = torch.empty(N, dtype=torch.float64, device=dev)
+                    g.fields_device(rho, u, T)
+                    g.sync()
+                    fields = (rho, u, T)
+                if t >= t_end:
+                    break
+                k = min(every, (steps if t < steps else t_end) - t)
+                t0 = time.perf_counter()
+                g.step(k)
+                g.sync()
+                wall += time.perf_counter() - t0
+                t += k
+        except E.ElbmError:
+            pass
+        finally:
+            g.close()
+            del g
+            torch.cuda.empty_cache()
+        return dict(hist=np.array(hist), fields=fields, physical_to=last_ok, s_per_step=wall / max(t, 1))
+
+    ref = run("f64")
+    if ref["fields"] is None:
+        raise RuntimeError(f"the FP64 run turned non-physical before step {steps} (last physical: "
+                           f"{ref['physical_to']})")
+    r_rho, r_u, r_T = ref["fields"]
+    hr = ref["hist"]
+    out = {"n": n, "steps": steps, "mu0": c.mu0, "every": every,
+           "f64": {"s_per_step": ref["s_per_step"], "physical_to": ref["physical_to"],
+                   "K": hr[:, 1].tolist(), "theta_rms": hr[:, 2].tolist()}}
+    for store in stores:
+        r = run(store)
+        e = {"s_per_step": r["s_per_step"], "physical_to": r["physical_to"]}
+        if r["fields"] is not None:
+            rho, u, T = r["fields"]
+            e.update(rho=_rel_l2(rho, r_rho), u=_rel_l2(u, r_u), T=_rel_l2(T, r_T),
+                     rho_fluct=_rel_l2(rho - rho.mean(), r_rho - r_rho.mean()),
+                     T_fluct=_rel_l2(T - T.mean(), r_T - r_T.mean()))
+            m = min(len(r["hist"]), len(hr))
+            h = r["hist"][:m]
+            dK = np.abs(h[:, 1] - hr[:m, 1]) / hr[:m, 1]
+            dth = np.abs(h[:, 2] - hr[:m, 2]) / hr[:m, 2]
+            upto = h[:, 0] <= steps
+            e["K_dev"] = dK.tolist()
+            e["theta_dev"] = dth.tolist()
+            e["K_drift"] = float(np.max(dK[1:][upto[1:]])) if m > 1 else 0.0
+            e["theta_drift"] = float(np.max(dth[1:][upto[1:]])) if m > 1 else 0.0
+            del rho, u, T
+        r["fields"] = None
+        torch.cuda.empty_cache()
+        out[store] = e
+    return out
