@@ -271,14 +271,17 @@ def _center_after_one_step(c, x, y, z):
     return r[k], u[:, k], T[k]
 
 
+@pytest.mark.parametrize("kernel", [0, 3])
 @pytest.mark.parametrize("store,tol,drift", [("f32", 2e-6, 1e-6), ("f16dev", 2e-4, 1e-5)])
-def test_full_size_256_sampled_nodes(E, store, tol, drift):
-    """At the bench's full size (D3Q27, 256^3, decaying-turbulence field, fused kernel)
-    sampled nodes after one step equal the oracle's one-by-one values, and the
-    totals are conserved over 5 steps (FP16: up to the storage rounding, 2^-11 of
-    deviations that are a few percent of the populations)."""
+def test_full_size_256_sampled_nodes(E, store, tol, drift, kernel):
+    """At the bench's full size (D3Q27, 256^3, decaying-turbulence field; the fused
+    cp.async kernel the bench times, and the bulk-copy one) sampled nodes after one
+    step equal the oracle's one-by-one values, and the totals are conserved over 5
+    steps (FP16: up to the storage rounding, 2^-11 of deviations that are a few
+    percent of the populations)."""
     c = C.hit(256, seed=20210218)
     g = E.Solver.from_case(c, store=store)
+    g.set_kernel(kernel)
     t0 = g.conservation()
     g.step(1)
     rho, u, T = g.fields()
