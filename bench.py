@@ -39,8 +39,8 @@ METRIC = "D3Q27 two-pop GLUPS at 256^3: FP16-store vs FP32 vs FP64; % of HBM roo
 WORKLOAD = "D3Q27 decaying compressible turbulence 256^3, periodic, Ma_t=0.5, Re_lambda=72"
 FALLBACK_HBM_GBS = 6800.0
 # step schedules (elbm_kernel): one fused kernel, two passes, fused with the plane
-# gathered twice, fused with bulk-copy (TMA) plane staging
-KERNELS = {"fused": 0, "twopass": 1, "reread": 2, "bulk": 3}
+# gathered twice, fused with tensor-copy (TMA) plane staging
+KERNELS = {"fused": 0, "twopass": 1, "reread": 2, "tma": 3}
 
 
 def _dist():

@@ -85,15 +85,17 @@ typedef enum {
     ELBM_KERNEL_TWOPASS = 1,      /* moment/Q~ pass into the aux buffer, then collide+stream */
     ELBM_KERNEL_FUSED_REREAD = 2, /* one kernel, D3Q27 plane gathered twice (second from L2);
                                      D2Q9 runs the fused kernel */
-    ELBM_KERNEL_FUSED_BULK = 3    /* one kernel, D3Q27 FP32/FP16/BF16: the rows of each plane
-                                     are copied into shared memory by the bulk asynchronous
-                                     copy engine (TMA), completion counted on an mbarrier.
-                                     Needs a periodic x axis with nx a multiple of 2 (FP32)
-                                     or 4 (FP16/BF16) and nx >= 36 (FP32) or 40; otherwise
-                                     elbm_set_kernel returns ELBM_ERR_UNSUPPORTED.  Its
-                                     waits are bounded (about 1 s): one that gives up is
-                                     reported as ELBM_ERR_TIMEOUT by the next
-                                     synchronising call */
+    ELBM_KERNEL_FUSED_TMA = 3     /* one kernel, D3Q27 FP32/FP16/BF16: each plane is staged in
+                                     shared memory by the tensor-copy engine (TMA), one box per
+                                     direction, where the boxes of a tile lie inside the grid,
+                                     and by per-pair cp.async copies at the x and y faces; a
+                                     plane's arrival is counted on an mbarrier.  Needs nx a
+                                     multiple of 2 (FP32) or 4 (FP16/BF16), otherwise
+                                     elbm_set_kernel returns ELBM_ERR_UNSUPPORTED (also
+                                     returned by elbm_step if the driver refused the tensor
+                                     maps at elbm_bind).  Its waits are bounded (about 1 s):
+                                     one that gives up is reported as ELBM_ERR_TIMEOUT by the
+                                     next synchronising call */
 } elbm_kernel;
 
 typedef struct {

@@ -22,6 +22,8 @@ struct elbm_handle {
     size_t pop_bytes;
     AuxLayout aux;
     void* pop[2];
+    CUtensorMap tmap[2];     // tensor maps of pop[0], pop[1] (TMA-staged D3Q27 kernel)
+    bool tmap_ready;
     char* auxp;
     cudaStream_t stream;
     bool bound;
@@ -189,6 +191,10 @@ int elbm_bind(elbm_handle* h, void* pop_a, void* pop_b, void* aux, void* stream)
     if (((uintptr_t)pop_a | (uintptr_t)pop_b | (uintptr_t)aux) % kAlign) return ELBM_ERR_ARG;
     h->pop[0] = pop_a;
     h->pop[1] = pop_b;
+    h->tmap_ready = false;
+    if (h->ops->tma_supported(h->kp))
+        h->tmap_ready = h->ops->encode_tmap(h->kp, pop_a, &h->tmap[0]) == 1 &&
+                        h->ops->encode_tmap(h->kp, pop_b, &h->tmap[1]) == 1;
     h->auxp = (char*)aux;
     h->stream = (cudaStream_t)stream;
     h->cur = 0;
@@ -231,9 +237,11 @@ int elbm_step(elbm_handle* h, int nsteps) {
         else if (h->kernel == ELBM_KERNEL_FUSED_REREAD)
             e = h->ops->step_fused_reread(h->kp, src, dst, step_partials(h), &h->step_blocks, status_ptr(h),
                                           h->stream, &h->launches);
-        else if (h->kernel == ELBM_KERNEL_FUSED_BULK)
-            e = h->ops->step_fused_bulk(h->kp, src, dst, step_partials(h), &h->step_blocks, status_ptr(h),
-                                        h->stream, &h->launches);
+        else if (h->kernel == ELBM_KERNEL_FUSED_TMA) {
+            if (!h->tmap_ready) return ELBM_ERR_UNSUPPORTED;
+            e = h->ops->step_fused_tma(h->kp, src, dst, &h->tmap[h->cur], step_partials(h), &h->step_blocks,
+                                       status_ptr(h), h->stream, &h->launches);
+        }
         else
             e = h->ops->step_fused(h->kp, src, dst, step_partials(h), &h->step_blocks, status_ptr(h), h->stream,
                                    &h->launches);
@@ -309,9 +317,9 @@ int elbm_step_totals(elbm_handle* h, double out[5]) {
 
 int elbm_set_kernel(elbm_handle* h, int kernel) {
     if (!h || (kernel != ELBM_KERNEL_FUSED && kernel != ELBM_KERNEL_TWOPASS && kernel != ELBM_KERNEL_FUSED_REREAD &&
-               kernel != ELBM_KERNEL_FUSED_BULK))
+               kernel != ELBM_KERNEL_FUSED_TMA))
         return ELBM_ERR_ARG;
-    if (kernel == ELBM_KERNEL_FUSED_BULK && !h->ops->bulk_supported(h->kp)) return ELBM_ERR_UNSUPPORTED;
+    if (kernel == ELBM_KERNEL_FUSED_TMA && !h->ops->tma_supported(h->kp)) return ELBM_ERR_UNSUPPORTED;
     h->kernel = kernel;
     return ELBM_OK;
 }

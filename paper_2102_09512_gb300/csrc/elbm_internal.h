@@ -2,6 +2,7 @@
 // units (elbm_kernels.cu, compiled once per lattice x store kind).
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (type only; the library does not link the driver)
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -228,9 +229,11 @@ struct Ops {
                          long long* launches);   // kStatsSums partial sums per CTA
     int fused_tile_y;             // tile height of the fused kernels (tile width 32)
     int (*fused_occupancy)();     // resident CTAs per SM of the default fused D3Q27 kernel (0: unknown)
-    cudaError_t (*step_fused_bulk)(const KParams& p, const void* src, void* dst, double* partials,
-                                   int* nblocks, int* status, cudaStream_t s, long long* launches);
-    int (*bulk_supported)(const KParams& p);   // the grid suits the bulk-staged D3Q27 kernel
+    cudaError_t (*step_fused_tma)(const KParams& p, const void* src, void* dst, const CUtensorMap* src_map,
+                                  double* partials, int* nblocks, int* status, cudaStream_t s, long long* launches);
+    int (*tma_supported)(const KParams& p);   // the grid suits the TMA-staged D3Q27 kernel
+    // tensor map of a store for that kernel: 1 made, 0 not applicable, -1 the driver refused
+    int (*encode_tmap)(const KParams& p, const void* base, CUtensorMap* out);
 };
 
 // z-segment length of the fused D3Q27 kernels.  Each CTA marches one (tile, segment)

@@ -19,6 +19,8 @@
 // Streaming is "pull": the pair of direction i at node x is read from x - c_i of the
 // source store and the post-collision pair is written at x in the destination store
 // (ping-pong), so every store is coalesced and no two threads write one element.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -802,11 +804,11 @@ fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPla
 }
 
 // ---------------------------------------------------------------------------
-// D3Q27 with bulk-copy plane staging
+// D3Q27 with tensor-copy (TMA) plane staging
 // ---------------------------------------------------------------------------
-// The bulk asynchronous copy engine (cp.async.bulk, the TMA unit) moves whole rows of
-// a direction plane from global to shared memory; the copies of one plane count
-// their bytes on an mbarrier, which the consuming threads wait on.
+// The tensor-copy engine (cp.async.bulk.tensor, the TMA unit) moves a box of a direction
+// plane from global to shared memory; the copies of one plane count their bytes on an
+// mbarrier, which the consuming threads wait on.
 __device__ __forceinline__ unsigned smem_u32(const void* ptr) {
     return static_cast<unsigned>(__cvta_generic_to_shared(ptr));
 }
@@ -819,6 +821,11 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
                  "r"(bytes)
                  : "memory");
+}
+// One arrival, made when this thread's earlier cp.async copies have landed (counts as
+// one of the arrivals the mbarrier was initialised with).
+__device__ __forceinline__ void mbar_arrive_cp_async(unsigned bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
     unsigned ok;
@@ -843,65 +850,70 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
         if (global_ns() - t0 > 1000000000ull) return false;
     return true;
 }
-// Orders this thread's earlier shared-memory accesses before later async-proxy writes.
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) into shared
-// memory, completing on the mbarrier.
-__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                     dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
+// Box {x, y, w} of a rank-3 tensor map into shared memory (128-byte aligned), completing
+// on the mbarrier.  x * element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int x, int y, int w,
+                                            unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(w), "r"(bar)
+        : "memory");
 }
 
-// Shared-memory plan of the bulk-staged kernel.  For every direction i the buffer of
+// Shared-memory plan of the TMA-staged kernel.  For every direction i the buffer of
 // plane q holds a box of RB rows x BW columns of the SOURCE plane q - c_z: rows
 // y0 - 1 - c_y ... y0 + TY - c_y and columns x0 - XO ... x0 + TX + XO - 1, so that node
 // (x, y) of the tile and its halo ring finds its pulled pair of direction i at box row
-// y - y0 + 1 and column x - x0 + XO - c_x.  XO keeps every row copy 16-byte aligned.
+// y - y0 + 1 and column x - x0 + XO - c_x (one box element per destination node and
+// direction).  XO keeps the box's first column 16-byte aligned; each box starts on a
+// 128-byte boundary (BOXP elements apart).
 template <int TY>
-struct Bulk {
+struct Tma {
     static constexpr int XO = 16 / (int)sizeof(P);
     static constexpr int BW = TX + 2 * XO;
     static constexpr int RB = TY + 2;
     static constexpr int BOX = RB * BW;
-    static constexpr unsigned plane_bytes = (unsigned)(Q * BOX * sizeof(P));
-    static constexpr size_t buf_bytes = (size_t)2 * plane_bytes;
+    static constexpr int BOXP = ((BOX * (int)sizeof(P) + 127) / 128) * 128 / (int)sizeof(P);
+    static constexpr unsigned plane_bytes = (unsigned)(Q * BOX * sizeof(P));   // bytes the 27 boxes deliver
+    static constexpr size_t buf_bytes = (size_t)2 * Q * BOXP * sizeof(P);
     static constexpr size_t q_bytes = (size_t)2 * (TY * (TX + 2) + (TY + 2) * TX) * sizeof(R);
     static constexpr size_t smem_bytes = buf_bytes + q_bytes + 2 * sizeof(unsigned long long);
-    static constexpr int NTASK = Q * RB;   // row copies per plane
 };
 
-// D3Q27, pipelined on bulk copies.  The same march as fused3d_kernel (a TX x TY column
-// over a z segment, two plane buffers, plane z+2 requested while plane z+1's moments
-// and plane z's collision run), but the pulled pairs arrive as row copies issued by
-// threads NH.. (about one copy per thread per plane instead of 27 per-pair copies),
-// and a plane's completion is one mbarrier phase.  Per plane z:
+// D3Q27, pipelined on tensor copies.  The same march as fused3d_kernel (a TX x TY
+// column over a z segment, two plane buffers, plane z+2 requested while plane z+1's
+// moments and plane z's collision run), with a plane's arrival counted on one mbarrier.
+// A CTA whose boxes lie inside the grid for every direction requests a plane as 27
+// tensor copies (one box per direction, issued by six threads of each of warps 3..7)
+// and one thread announces their bytes; a CTA at an x or y face, where a box would wrap
+// around a periodic axis or clamp at a zero-gradient one, copies each pulled pair with
+// cp.async into the same box positions (the boundary map resolves the source), and each
+// thread arrives when its copies have landed.  Per plane z:
 //   wait for plane z+1's phase; read the pairs of plane z into registers; barrier
 //   (every thread has read plane z's buffer; the Q~ arrays are free); request plane
 //   z+2 into plane z's buffer; moments of plane z+1 (tile and halo) -> Q~; collide
 //   plane z and store.
 // A wait that gives up (about one second) latches kStatusTimeoutBit, and the CTA stops
 // after waiting, again bounded, for the copies it still has in flight.
-// It is a selectable schedule, not the default: a plane is about 300 row copies of
-// 160-288 bytes, and their per-copy cost in the copy engine, not the bytes, sets the
-// pace (at 256^3 it reaches about 3/4 of fused3d_kernel's rate; with one warp issuing
-// all copies instead of six, a third of it).  Each copy is one bulk operation because
-// the pulled window of a direction is a box of short rows; one copy per box would need
-// a tensor map and a separate path for the tiles whose box wraps around the grid.
+// A selectable schedule: at 256^3 it matches fused3d_kernel in FP32 and runs 2 % slower
+// with FP16 pairs.  It executes 6 % fewer instructions and waits far less at the plane
+// barrier, but the boxes carry 11-19 % more pairs than the pulls use (corners, and the
+// columns that keep the box 16-byte aligned) and the kernel draws more DRAM reads.
 template <int TY, int MINB, int DD, bool CAL>
 __global__ void __launch_bounds__(TX * TY, MINB)
-fused3d_bulk_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPlanes pl,
-                    const P* __restrict__ src, double* __restrict__ partials, int* __restrict__ status) {
-    using BB = Bulk<TY>;
-    static_assert(sizeof(R) == 4 && DD == 3, "the bulk-staged kernel is D3Q27 in FP32 arithmetic");
-    constexpr int NT = TX * TY, NH = 2 * TX + 2 * TY, XO = BB::XO, BW = BB::BW, RB = BB::RB, BOX = BB::BOX;
-    static_assert(NT > NH, "row copies are issued by the threads without a halo node");
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    P* buf = reinterpret_cast<P*>(smem_raw);                                // [2][Q][RB][BW]
-    R* qxs = reinterpret_cast<R*>(smem_raw + BB::buf_bytes);                // [2][TY][TX+2]
+fused3d_tma_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPlanes pl,
+                   const __grid_constant__ CUtensorMap tmap, const P* __restrict__ src,
+                   double* __restrict__ partials, int* __restrict__ status) {
+    using TT = Tma<TY>;
+    static_assert(sizeof(R) == 4 && DD == 3, "the TMA-staged kernel is D3Q27 in FP32 arithmetic");
+    constexpr int NT = TX * TY, NH = 2 * TX + 2 * TY, XO = TT::XO, BW = TT::BW, BOXP = TT::BOXP;
+    static_assert(NT >= 96 + 5 * 32, "tensor copies are issued by warps 3..7");
+    extern __shared__ __align__(128) unsigned char tma_smem[];   // tensor-copy destinations: 128-byte aligned
+    P* buf = reinterpret_cast<P*>(tma_smem);                                // [2][Q][BOXP]
+    R* qxs = reinterpret_cast<R*>(tma_smem + TT::buf_bytes);                // [2][TY][TX+2]
     R* qys = qxs + 2 * TY * (TX + 2);                                       // [2][TY+2][TX]
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + BB::buf_bytes + BB::q_bytes);
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(tma_smem + TT::buf_bytes + TT::q_bytes);
     auto QX = [&](int b, int row, int col) -> R& { return qxs[(b * TY + row) * (TX + 2) + col]; };
     auto QY = [&](int b, int row, int col) -> R& { return qys[(b * (TY + 2) + row) * TX + col]; };
 
@@ -912,66 +924,67 @@ fused3d_bulk_kernel(const __grid_constant__ KParams p, const __grid_constant__ D
     const bool active = x < p.nx && y < p.ny;
     const int xl = min(x0 + TX, p.nx) - 1 - x0, yl = min(y0 + TY, p.ny) - 1 - y0;
     const int nslot = (ty + 1) * BW + tx + XO;   // this node in a direction's box (before -c_x)
+    // every box of this CTA inside the grid: columns x0 - XO .. x0 + TX + XO - 1, rows
+    // y0 - 2 .. y0 + TY + 1 (the union over c_y)
+    const bool boxed = x0 >= XO && x0 + TX + XO <= p.nx && y0 >= 2 && y0 + TY + 1 < p.ny;
 
-    // this thread's halo node: its box position is the unmapped one on a periodic axis
-    // and the mapped (clamped) node's on a zero-gradient axis
+    // this thread's halo node: its box position is the unmapped one, or, beyond a
+    // zero-gradient face, that of the clamped node it copies (whose pairs the tile node
+    // there already brings: such a halo thread copies nothing)
     int hx = 0, hy = 0, hsx = 0, hsy = 0, haxis = 0, hslot = 0;
     const bool has_halo = tid < NH && halo_node<TY>(p, tid, x0, y0, xl, yl, hx, hy, hsx, hsy, haxis);
+    bool halo_copies = false;
     if (has_halo) {
         const int ux = haxis == 1 ? x0 + hsx : x0 + hsx - 1;
         const int uy = haxis == 1 ? y0 + hsy - 1 : y0 + hsy;
-        hslot = ((p.per_y ? uy : hy) - y0 + 1) * BW + (ux - x0 + XO);
+        const bool clamped = (ux < 0 || ux >= p.nx) ? !p.per_x : ((uy < 0 || uy >= p.ny) ? !p.per_y : false);
+        halo_copies = !clamped;
+        hslot = ((clamped ? hy : uy) - y0 + 1) * BW + ((clamped ? hx : ux) - x0 + XO);
     }
 
-    // row copies of source plane q - c_z for every direction into buffer sb; thread 0
-    // announces the plane's bytes (a phase completes when they have all landed)
     unsigned issued = 0u;   // planes requested per buffer: buffer 0 in the low half, 1 in the high
     auto issue_plane = [&](int q, int sb) {
         const unsigned bar = smem_u32(&bars[sb]);
         issued += sb ? 0x10000u : 1u;
-        if (tid == 0) mbar_expect_tx(bar, BB::plane_bytes);
-        if (tid >= NH) {
-            fence_proxy_async();
-            for (int t = tid - NH; t < BB::NTASK; t += NT - NH) {
-                const int i = t / RB, r = t - RB * i;
+        P* bb = buf + (size_t)sb * Q * BOXP;
+        if (boxed) {
+            if (tid == 0) mbar_expect_tx(bar, TT::plane_bytes);
+            const int w = (tid >> 5) - 3, lane = tid & 31;
+            if (w >= 0 && lane < 6 && 6 * w + lane < Q) {
+                const int i = 6 * w + lane;
                 const int b = (i / 3) % 3, c = i / 9;
-                int ys = y0 + r - b;   // y0 - 1 - c_y + r
-                if (p.per_y) {   // ys is in [y0 - 2, y0 + TY + 1]: a few periods at most
-                    while (ys < 0) ys += p.ny;
-                    while (ys >= p.ny) ys -= p.ny;
-                } else {
-                    ys = min(max(ys, 0), p.ny - 1);
-                }
                 const int zs = map_axis(q + 1 - c, p.nz, p.per_z);   // q - c_z
-                const P* row = pl.src[i] + (unsigned)(p.nx * (ys + p.ny * zs));
-                const unsigned d = smem_u32(buf + ((size_t)sb * Q + i) * BOX + r * BW);
-                const int xs = x0 - XO;
-                if (xs < 0) {   // columns -XO .. -1 are the last XO of the row
-                    bulk_g2s(d, row + (p.nx - XO), XO * sizeof(P), bar);
-                    bulk_g2s(d + XO * sizeof(P), row, (BW - XO) * sizeof(P), bar);
-                } else if (xs + BW > p.nx) {   // columns nx .. wrap to 0 ..
-                    const int n1 = p.nx - xs;
-                    bulk_g2s(d, row + xs, n1 * sizeof(P), bar);
-                    bulk_g2s(d + n1 * sizeof(P), row, (BW - n1) * sizeof(P), bar);
-                } else {
-                    bulk_g2s(d, row + xs, BW * sizeof(P), bar);
-                }
+                tma_load_3d(smem_u32(bb + (size_t)i * BOXP), &tmap, x0 - XO, y0 - b, i * p.nz + zs, bar);
             }
+        } else {
+            if (active) {
+                PullRows r;
+                pull_rows(p, x, y, q, r);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) cp_async<sizeof(P)>(bb + i * BOXP + nslot - cx_of(i), dir_src(pl, r, i));
+            }
+            if (halo_copies) {
+                PullRows r;
+                pull_rows(p, hx, hy, q, r);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) cp_async<sizeof(P)>(bb + i * BOXP + hslot - cx_of(i), dir_src(pl, r, i));
+            }
+            mbar_arrive_cp_async(bar);
         }
     };
     auto slot_moments = [&](int sb, int slot, Moments<R>& m, auto full) {
-        const P* bb = buf + (size_t)sb * Q * BOX + slot;
+        const P* bb = buf + (size_t)sb * Q * BOXP + slot;
         R f[Q], g[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) Cd::dec(bb[i * BOX - cx_of(i)], f[i], g[i]);
+        for (int i = 0; i < Q; ++i) Cd::dec(bb[i * BOXP - cx_of(i)], f[i], g[i]);
         node_moments<kD, R, decltype(full)::value, DEV, CAL>(f, g, p, m);
     };
     using Full = std::true_type;
     using Lite = std::false_type;
 
     if (tid == 0) {
-        mbar_init(smem_u32(&bars[0]), 1);
-        mbar_init(smem_u32(&bars[1]), 1);
+        mbar_init(smem_u32(&bars[0]), boxed ? 1 : NT);
+        mbar_init(smem_u32(&bars[1]), boxed ? 1 : NT);
     }
     __syncthreads();
 
@@ -1007,9 +1020,9 @@ fused3d_bulk_kernel(const __grid_constant__ KParams p, const __grid_constant__ D
         late |= !mbar_wait(smem_u32(&bars[sn]), ((k + 1) >> 1) & 1);
         P pk[Q];   // the pulled pairs of plane z, as stored
         if (active) {
-            const P* bb = buf + (size_t)sz * Q * BOX + nslot;
+            const P* bb = buf + (size_t)sz * Q * BOXP + nslot;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) pk[i] = bb[i * BOX - cx_of(i)];
+            for (int i = 0; i < Q; ++i) pk[i] = bb[i * BOXP - cx_of(i)];
         }
         if (__syncthreads_or(late)) {
             gave_up = true;
@@ -1062,6 +1075,7 @@ fused3d_bulk_kernel(const __grid_constant__ KParams p, const __grid_constant__ D
         }
         if (tid == 0) atomicOr(status, kStatusTimeoutBit);
     }
+    cp_async_wait_all();
     flag_if(bad, status);
     double tot[5];
 #pragma unroll
@@ -1184,17 +1198,42 @@ using PipeCfg = Pipe<kTY3, kNB>;
 #define ELBM_EARLY 1
 #endif
 constexpr bool kEarly = ELBM_EARLY && kMinB == 1;
-// Bulk-staged D3Q27 kernel: FP32 plane buffers (152 KB) leave room for one CTA per SM,
-// FP16/BF16 ones (84 KB) for two.
-using BulkCfg = Bulk<kTY3>;
-constexpr int kBulkMinB = (BulkCfg::smem_bytes * 2 + 4096 <= 228 * 1024) ? 2 : 1;
+// TMA-staged D3Q27 kernel: FP32 plane buffers (155 KB) leave room for one CTA per SM,
+// FP16/BF16 ones (88 KB) for two.
+using TmaCfg = Tma<kTY3>;
+constexpr int kTmaMinB = (TmaCfg::smem_bytes * 2 + 4096 <= 228 * 1024) ? 2 : 1;
 
-// Can the bulk-staged kernel run this grid?  x must be periodic (a row that leaves the
-// grid wraps around as a second copy), nx a multiple of XO (rows stay 16-byte aligned)
-// and at least one box wide (a row wraps at most once).
-int bulk_supported(const KParams& p) {
+// Can the TMA-staged kernel run this grid?  The tensor map's row pitch nx * pair size
+// must be a multiple of 16 bytes (nx a multiple of 2 for FP32 pairs, 4 for FP16/BF16).
+int tma_supported(const KParams& p) {
     if (kD != 3 || !kPipe) return 0;
-    return p.per_x && p.nx % BulkCfg::XO == 0 && p.nx >= BulkCfg::BW && !p.has_fixed;
+    return p.nx % TmaCfg::XO == 0 && !p.has_fixed;
+}
+
+// Tensor map of a population store as rank 3: x (nx pairs), y (ny), w = i * nz + z (the
+// planes of all directions), box TmaCfg::BW x RB x 1.  The encoder is the driver's,
+// reached through the runtime (no link against the driver library).
+int encode_tmap(const KParams& p, const void* base, CUtensorMap* out) {
+    if (!tma_supported(p)) return 0;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return -1;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny, (cuuint64_t)p.nz * Q};
+    const cuuint64_t strides[2] = {(cuuint64_t)p.nx * sizeof(P), (cuuint64_t)p.nx * p.ny * sizeof(P)};
+    const cuuint32_t box[3] = {(cuuint32_t)TmaCfg::BW, (cuuint32_t)TmaCfg::RB, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const CUtensorMapDataType dt = sizeof(P) == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+    const CUresult r = encode(out, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 1 : -1;
 }
 
 inline unsigned blocks_1d(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
@@ -1282,31 +1321,31 @@ cudaError_t launch_fused_cal(const KParams& p, const void* src, void* dst, doubl
 }
 
 template <int DD, bool CAL>
-cudaError_t launch_bulk_cal(const KParams& p, const void* src, void* dst, double* partials, int* status,
-                            cudaStream_t s) {
+cudaError_t launch_tma_cal(const KParams& p, const void* src, void* dst, const CUtensorMap* map, double* partials,
+                           int* status, cudaStream_t s) {
     if constexpr (DD == 3 && kPipe) {
-        auto kern = fused3d_bulk_kernel<kTY3, kBulkMinB, DD, CAL>;
+        auto kern = fused3d_tma_kernel<kTY3, kTmaMinB, DD, CAL>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)BulkCfg::smem_bytes);
+                                             (int)TmaCfg::smem_bytes);
         if (e != cudaSuccess) return e;
         DirPlanes pl;
         for (int i = 0; i < Q; ++i) {
             pl.src[i] = (const P*)src + (size_t)i * (size_t)p.N;
             pl.dst[i] = (P*)dst + (size_t)i * (size_t)p.N;
         }
-        kern<<<fused_grid(p), dim3(TX, kTY3), BulkCfg::smem_bytes, s>>>(p, pl, (const P*)src, partials, status);
+        kern<<<fused_grid(p), dim3(TX, kTY3), TmaCfg::smem_bytes, s>>>(p, pl, *map, (const P*)src, partials, status);
         return cudaGetLastError();
     } else {
         return cudaErrorInvalidValue;
     }
 }
 
-// Bulk-staged fused step (callers check bulk_supported first).
-cudaError_t launch_fused_bulk(const KParams& p, const void* src, void* dst, double* partials, int* nblocks,
-                              int* status, cudaStream_t s, long long* launches) {
-    if (!bulk_supported(p)) return cudaErrorInvalidValue;
-    const cudaError_t e = p.eos ? launch_bulk_cal<kD, true>(p, src, dst, partials, status, s)
-                                : launch_bulk_cal<kD, false>(p, src, dst, partials, status, s);
+// TMA-staged fused step; map is the tensor map of src (encode_tmap).
+cudaError_t launch_fused_tma(const KParams& p, const void* src, void* dst, const CUtensorMap* map,
+                             double* partials, int* nblocks, int* status, cudaStream_t s, long long* launches) {
+    if (!tma_supported(p) || !map) return cudaErrorInvalidValue;
+    const cudaError_t e = p.eos ? launch_tma_cal<kD, true>(p, src, dst, map, partials, status, s)
+                                : launch_tma_cal<kD, false>(p, src, dst, map, partials, status, s);
     ++*launches;
     const dim3 grid = fused_grid(p);
     *nblocks = (int)(grid.x * grid.y * grid.z);
@@ -1410,7 +1449,7 @@ int fused_occupancy() { return fused_occupancy_impl<kD>(); }
 const Ops kOps = {kD,          kST,           sizeof(P) / 2,  sizeof(R),            max_blocks,
                   launch_init, launch_fields, launch_twopass, launch_fused_default, launch_fused_reread,
                   launch_totals, launch_ensemble, ensemble_occupancy, launch_stats,
-                  kD == 3 ? kTY3 : kTY2, fused_occupancy, launch_fused_bulk, bulk_supported};
+                  kD == 3 ? kTY3 : kTY2, fused_occupancy, launch_fused_tma, tma_supported, encode_tmap};
 
 }  // namespace
 

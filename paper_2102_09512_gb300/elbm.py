@@ -24,7 +24,7 @@ ELBM_BC_PERIODIC, ELBM_BC_ZEROGRAD, ELBM_BC_FIXED = 0, 1, 2
 ELBM_EOS_GAMMA, ELBM_EOS_CV_POLY = 0, 1
 ELBM_F64, ELBM_F32, ELBM_F16DEV, ELBM_BF16DEV = 0, 1, 2, 3
 ELBM_DERIV_UPWIND, ELBM_DERIV_CENTRAL = 0, 1
-ELBM_KERNEL_FUSED, ELBM_KERNEL_TWOPASS, ELBM_KERNEL_FUSED_REREAD, ELBM_KERNEL_FUSED_BULK = 0, 1, 2, 3
+ELBM_KERNEL_FUSED, ELBM_KERNEL_TWOPASS, ELBM_KERNEL_FUSED_REREAD, ELBM_KERNEL_FUSED_TMA = 0, 1, 2, 3
 ELBM_ENSEMBLE_PERSISTENT, ELBM_ENSEMBLE_PER_INSTANCE = 0, 1
 
 STORES = {"f64": ELBM_F64, "f32": ELBM_F32, "f16dev": ELBM_F16DEV, "bf16dev": ELBM_BF16DEV}

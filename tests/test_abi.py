@@ -115,26 +115,25 @@ def test_caloric_eos_is_validated(L):
     assert ei.value.code == L.ELBM_ERR_ARG
 
 
-def test_bulk_schedule_eligibility(L):
-    """The bulk-staged D3Q27 schedule needs FP32/FP16/BF16 pairs, a periodic x axis,
-    nx a multiple of 2 (FP32) or 4 (FP16/BF16) and nx >= 36 (FP32) or 40 (host-only
-    check in elbm_set_kernel)."""
-    ok = [(64, "f32"), (36, "f32"), (38, "f32"), (40, "f16dev"), (48, "bf16dev")]
-    bad = [(37, "f32"), (34, "f32"), (42, "f16dev"), (36, "f16dev"), (64, "f64")]
-    for nx, store in ok:
-        h = L.elbm_create(L.make_params(3, nx, 12, 10, store=store))
-        L.elbm_set_kernel(h, L.ELBM_KERNEL_FUSED_BULK)
+def test_tma_schedule_eligibility(L):
+    """The TMA-staged D3Q27 schedule needs FP32/FP16/BF16 pairs and nx a multiple of 2
+    (FP32) or 4 (FP16/BF16), the tensor map's row pitch being a multiple of 16 bytes; any
+    boundary types (host-only check in elbm_set_kernel)."""
+    ok = [(64, "f32", (0,) * 6), (38, "f32", (1,) * 6), (6, "f32", (0,) * 6), (40, "f16dev", (1, 1, 0, 0, 1, 1)),
+          (48, "bf16dev", (0,) * 6)]
+    bad = [(37, "f32"), (42, "f16dev"), (38, "bf16dev"), (64, "f64")]
+    for nx, store, bc in ok:
+        h = L.elbm_create(L.make_params(3, nx, 12, 10, store=store, bc=bc))
+        L.elbm_set_kernel(h, L.ELBM_KERNEL_FUSED_TMA)
         L.elbm_destroy(h)
     for nx, store in bad:
         h = L.elbm_create(L.make_params(3, nx, 12, 10, store=store))
         with pytest.raises(L.ElbmError) as ei:
-            L.elbm_set_kernel(h, L.ELBM_KERNEL_FUSED_BULK)
+            L.elbm_set_kernel(h, L.ELBM_KERNEL_FUSED_TMA)
         assert ei.value.code == L.ELBM_ERR_UNSUPPORTED, (nx, store)
         L.elbm_destroy(h)
-    for params in (L.make_params(3, 64, 12, 10, store="f32", bc=(1, 1, 0, 0, 0, 0)),
-                   L.make_params(2, 64, 12, 1, store="f32")):
-        h = L.elbm_create(params)
-        with pytest.raises(L.ElbmError) as ei:
-            L.elbm_set_kernel(h, L.ELBM_KERNEL_FUSED_BULK)
-        assert ei.value.code == L.ELBM_ERR_UNSUPPORTED
-        L.elbm_destroy(h)
+    h = L.elbm_create(L.make_params(2, 64, 12, 1, store="f32"))
+    with pytest.raises(L.ElbmError) as ei:
+        L.elbm_set_kernel(h, L.ELBM_KERNEL_FUSED_TMA)
+    assert ei.value.code == L.ELBM_ERR_UNSUPPORTED
+    L.elbm_destroy(h)

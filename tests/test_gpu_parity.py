@@ -413,66 +413,71 @@ def test_caloric_eos_parity(E, D, kernel, store):
 
 
 # --------------------------------------------------------------------------
-# D3Q27 schedule with bulk-copy (TMA) plane staging: ELBM_KERNEL_FUSED_BULK
+# D3Q27 schedule with tensor-copy (TMA) plane staging: ELBM_KERNEL_FUSED_TMA
 # --------------------------------------------------------------------------
-BULK_CASES = {
-    # periodic, 48 = 32 + 16: the second x tile is ragged and its box rows wrap to x = 0
-    "periodic": lambda: C.random_smooth(3, 48, 21, 19, seed=25, mu0=0.01, du=0.05, u0=U0_3D),
-    # x periodic, zero-gradient y and z faces (the halo rows read the clamped node's box row)
+TMA_CASES = {
+    # periodic; tiles (32, 8) and (32, 16) take the tensor-copy path, the others (at the
+    # x and y faces, or ragged) the per-pair cp.async path
+    "periodic": lambda: C.random_smooth(3, 80, 27, 13, seed=25, mu0=0.01, du=0.05, u0=U0_3D),
+    # zero-gradient on every face, with tensor-copy tiles inside
+    "zerograd": lambda: C.random_smooth(3, 72, 26, 11, seed=28, mu0=0.01, du=0.05, u0=U0_3D,
+                                        bc=(1, 1, 1, 1, 1, 1)),
+    # x periodic, zero-gradient y and z faces, every tile at a face (cp.async path only)
     "zerograd-yz": lambda: C.random_smooth(3, 40, 13, 17, seed=26, mu0=0.01, du=0.05, u0=U0_3D,
                                            bc=(0, 0, 1, 1, 1, 1)),
-    # fewer rows than a box (5 < 10): a box row index wraps more than once
+    # fewer rows than a box (5 < 10)
     "thin-y": lambda: C.random_smooth(3, 64, 5, 9, seed=27, mu0=0.01, du=0.05, u0=U0_3D),
 }
-BULK_STORES = ["f32", "f16dev", "bf16dev"]
+TMA_STORES = ["f32", "f16dev", "bf16dev"]
 
 
-@pytest.mark.parametrize("store", BULK_STORES)
-@pytest.mark.parametrize("case", list(BULK_CASES))
-def test_d3q27_bulk_parity(E, case, store):
-    c = BULK_CASES[case]()
+@pytest.mark.parametrize("store", TMA_STORES)
+@pytest.mark.parametrize("case", list(TMA_CASES))
+def test_d3q27_tma_parity(E, case, store):
+    c = TMA_CASES[case]()
     steps = 40
-    ref = oracle_fields(("bulk", case), c, steps)
-    got = gpu_fields(E, c, steps, store, E.ELBM_KERNEL_FUSED_BULK)
+    ref = oracle_fields(("tma", case), c, steps)
+    got = gpu_fields(E, c, steps, store, E.ELBM_KERNEL_FUSED_TMA)
     assert_parity(got, ref, TOL[store], (case, store))
 
 
 @pytest.mark.parametrize("store", ["f32", "f16dev"])
 @pytest.mark.parametrize("tz", [1, 2, 5])
-def test_d3q27_bulk_z_segments(E, tz, store):
+def test_d3q27_tma_z_segments(E, tz, store):
     """Segments of 1 and 2 planes run only the prologue and the last-plane paths of
-    the bulk pipeline."""
-    c = BULK_CASES["periodic"]()
-    ref = oracle_fields(("bulk", "periodic"), c, 40)
-    got = gpu_fields(E, c, 40, store, E.ELBM_KERNEL_FUSED_BULK, tz=tz)
+    the TMA pipeline."""
+    c = TMA_CASES["periodic"]()
+    ref = oracle_fields(("tma", "periodic"), c, 40)
+    got = gpu_fields(E, c, 40, store, E.ELBM_KERNEL_FUSED_TMA, tz=tz)
     assert_parity(got, ref, TOL[store], (tz, store))
 
 
-@pytest.mark.parametrize("store", BULK_STORES)
-def test_d3q27_bulk_caloric_eos(E, store):
-    c = BULK_CASES["periodic"]()
+@pytest.mark.parametrize("store", TMA_STORES)
+def test_d3q27_tma_caloric_eos(E, store):
+    c = TMA_CASES["periodic"]()
     c.cv = CV_POLY
-    ref = oracle_fields(("bulk-caloric",), c, 60)
-    got = gpu_fields(E, c, 60, store, E.ELBM_KERNEL_FUSED_BULK)
+    ref = oracle_fields(("tma-caloric",), c, 60)
+    got = gpu_fields(E, c, 60, store, E.ELBM_KERNEL_FUSED_TMA)
     assert_parity(got, ref, TOL[store], store)
 
 
-def test_d3q27_bulk_agrees_with_cp_async_kernel(E):
-    """The bulk-staged and the per-pair cp.async schedules run the same per-node
+def test_d3q27_tma_agrees_with_cp_async_kernel(E):
+    """The TMA-staged and the per-pair cp.async schedules run the same per-node
     arithmetic on the same pulled values."""
-    c = BULK_CASES["periodic"]()
-    for store, tol in (("f32", 1e-6), ("f16dev", TOL["f16dev"])):
-        a = gpu_fields(E, c, 20, store, E.ELBM_KERNEL_FUSED)
-        b = gpu_fields(E, c, 20, store, E.ELBM_KERNEL_FUSED_BULK)
-        for x, y in zip(a, b):
-            assert rel_l2(x, y) <= tol, store
+    for case in ("periodic", "zerograd"):
+        c = TMA_CASES[case]()
+        for store, tol in (("f32", 1e-6), ("f16dev", TOL["f16dev"])):
+            a = gpu_fields(E, c, 20, store, E.ELBM_KERNEL_FUSED)
+            b = gpu_fields(E, c, 20, store, E.ELBM_KERNEL_FUSED_TMA)
+            for x, y in zip(a, b):
+                assert rel_l2(x, y) <= tol, (case, store)
 
 
-def test_d3q27_bulk_step_totals(E):
-    """The totals the bulk kernel accumulates equal those of the state it produced."""
-    c = BULK_CASES["periodic"]()
+def test_d3q27_tma_step_totals(E):
+    """The totals the TMA kernel accumulates equal those of the state it produced."""
+    c = TMA_CASES["periodic"]()
     g = E.Solver.from_case(c, store="f32")
-    g.set_kernel(E.ELBM_KERNEL_FUSED_BULK)
+    g.set_kernel(E.ELBM_KERNEL_FUSED_TMA)
     g.step(3)
     t = g.step_totals()
     ref = g.conservation()
