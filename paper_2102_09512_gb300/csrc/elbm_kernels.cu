@@ -523,7 +523,7 @@ __device__ __forceinline__ void fused2d_tile(const KParams& p, const P* __restri
         const int h = tx + TX * ty;
         if (h < 2 * TX + 2 * TY && halo_node<TY>(p, h, x0, y0, xl, yl, hx, hy, sx, sy, axis)) {
             R q;
-            // the unmapped halo coordinate is (x0 + sx - 1, y0 + sy - 1) for columns and
+            // the unmapped halo coordinate is (x0 + sx - 1, y0 + sy) for columns and
             // (x0 + sx, y0 + sy - 1) for rows
             if (p.has_fixed && (axis == 1 ? beyond_fixed(p, 1, y0 + sy - 1, p.ny)
                                           : beyond_fixed(p, 0, x0 + sx - 1, p.nx))) {
