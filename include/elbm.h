@@ -185,6 +185,15 @@ int elbm_set_populations(elbm_handle *h, const void *host_src);
 /* Synchronises the stream and returns the latched device status (and clears it). */
 int elbm_sync(elbm_handle *h);
 
+/* Fault injection for testing the failure path of ELBM_KERNEL_FUSED_TMA: with on = 1,
+ * every plane a tile requests by tensor copies announces 16 bytes more than the copies
+ * deliver, so the tile's bounded wait (about one second) runs out; the kernel then
+ * waits, again bounded, for its copies, ends the tile and latches the timeout, which the
+ * next synchronising call returns as ELBM_ERR_TIMEOUT.  The step's results are invalid;
+ * the handle and the CUDA context stay usable (set the fields again).  on = 0 restores
+ * normal operation.  No effect on the other schedules. */
+int elbm_inject_wait_timeout(elbm_handle *h, int on);
+
 /* Number of time steps taken since the last elbm_set_fields*. */
 long long elbm_steps_done(const elbm_handle *h);
 

@@ -352,6 +352,12 @@ int elbm_sync(elbm_handle* h) {
     return sync_status(h);
 }
 
+int elbm_inject_wait_timeout(elbm_handle* h, int on) {
+    if (!h || (on != 0 && on != 1)) return ELBM_ERR_ARG;
+    h->kp.inject_tx = on ? 16u : 0u;
+    return ELBM_OK;
+}
+
 long long elbm_steps_done(const elbm_handle* h) { return h ? h->steps : -1; }
 
 long long elbm_launch_count(const elbm_handle* h) { return h ? h->launches : -1; }

@@ -948,7 +948,7 @@ fused3d_tma_kernel(const __grid_constant__ KParams p, const __grid_constant__ Di
         issued += sb ? 0x10000u : 1u;
         P* bb = buf + (size_t)sb * Q * BOXP;
         if (boxed) {
-            if (tid == 0) mbar_expect_tx(bar, TT::plane_bytes);
+            if (tid == 0) mbar_expect_tx(bar, TT::plane_bytes + p.inject_tx);
             const int w = (tid >> 5) - 3, lane = tid & 31;
             if (w >= 0 && lane < 6 && 6 * w + lane < Q) {
                 const int i = 6 * w + lane;

@@ -46,6 +46,7 @@ struct KParams {
     double cvd[4], Ud[4];        // Cv(T) = sum cvd[k] T^k, U(T) = T sum Ud[k] T^k (Ud[k] = cvd[k]/(k+1))
     float cvf[4], Uf[4];
     int powlaw;                                            // mu_exp != 0
+    unsigned inject_tx;          // fault injection: extra bytes each TMA plane announces (0 in use)
     double d_Cv, d_invT0;
     float f_gm1, f_Cv, f_Pr, f_mu0, f_invT0, f_mu_exp;
 };

@@ -70,6 +70,7 @@ _SIGS = {
     "elbm_step_totals": (ctypes.c_int, [_vp, _dp]),
     "elbm_turbulence_stats": (ctypes.c_int, [_vp, _dp]),
     "elbm_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "elbm_inject_wait_timeout": (ctypes.c_int, [_vp, ctypes.c_int]),
     "elbm_set_tile_z": (ctypes.c_int, [_vp, ctypes.c_int]),
     "elbm_get_populations": (ctypes.c_int, [_vp, _vp]),
     "elbm_set_populations": (ctypes.c_int, [_vp, _vp]),
@@ -194,6 +195,10 @@ def elbm_turbulence_stats(h) -> dict:
 
 def elbm_set_kernel(h, kernel: int):
     _check(lib().elbm_set_kernel(h, int(kernel)), "elbm_set_kernel")
+
+
+def elbm_inject_wait_timeout(h, on: int):
+    _check(lib().elbm_inject_wait_timeout(h, int(on)), "elbm_inject_wait_timeout")
 
 
 def elbm_set_tile_z(h, tz: int):

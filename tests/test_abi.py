@@ -137,3 +137,13 @@ def test_tma_schedule_eligibility(L):
         L.elbm_set_kernel(h, L.ELBM_KERNEL_FUSED_TMA)
     assert ei.value.code == L.ELBM_ERR_UNSUPPORTED
     L.elbm_destroy(h)
+
+
+def test_wait_timeout_injection_arguments(L):
+    h = L.elbm_create(L.make_params(3, 64, 24, 8, store="f32"))
+    L.elbm_inject_wait_timeout(h, 1)
+    L.elbm_inject_wait_timeout(h, 0)
+    with pytest.raises(L.ElbmError) as ei:
+        L.elbm_inject_wait_timeout(h, 2)
+    assert ei.value.code == L.ELBM_ERR_ARG
+    L.elbm_destroy(h)

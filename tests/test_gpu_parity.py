@@ -483,3 +483,26 @@ def test_d3q27_tma_step_totals(E):
     ref = g.conservation()
     assert np.allclose(t, ref, rtol=1e-6, atol=1e-6 * abs(ref[0]))
     g.close()
+
+
+def test_tma_wait_timeout_is_reported_and_recoverable(E):
+    """Failure path of the TMA-staged schedule, exercised without a GPU fault: with the
+    fault injection on, the tile that requests its planes by tensor copies (the one at
+    (32, 8) of this 96 x 24 x 4 grid) waits for 16 bytes that never come.  Its bounded
+    waits run out (about a second each), the step reports ELBM_ERR_TIMEOUT at the next
+    synchronising call, and afterwards the same handle and context run normal steps
+    that match the oracle."""
+    c = C.random_smooth(3, 96, 24, 4, seed=29, mu0=0.01, du=0.05, u0=U0_3D)
+    g = E.Solver.from_case(c, store="f32")
+    g.set_kernel(E.ELBM_KERNEL_FUSED_TMA)
+    E.elbm_inject_wait_timeout(g.h, 1)
+    g.step(1)
+    with pytest.raises(E.ElbmError) as ei:
+        g.sync()
+    assert ei.value.code == E.ELBM_ERR_TIMEOUT
+    E.elbm_inject_wait_timeout(g.h, 0)
+    g.set_fields(c.rho, c.u, c.T)
+    g.step(10)
+    ref = oracle_fields(("tma-timeout",), c, 10)
+    assert_parity(g.fields(), ref, TOL["f32"])
+    g.close()
