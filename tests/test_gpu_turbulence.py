@@ -166,3 +166,17 @@ def test_reduced_precision_stores_against_gpu_fp64(E, n, steps, every):
             assert e[q] <= tol, (store, q, e[q])
         if store != "bf16dev":
             assert e["K_drift"] <= 0.01 and e["theta_drift"] <= 0.01, (store, e["K_drift"], e["theta_drift"])
+
+
+def test_long_run_statistics_128_2000_steps(E):
+    """Decaying turbulence at 128^3 (Ma_t = 0.5, Re_lambda = 72) over 2000 steps, while K
+    decays to about 1 % of K_0: every store stays physical and keeps K(t) and
+    theta_rms(t), sampled every 20 steps, within 1 % of the GPU FP64 run (measured:
+    FP32 0.008 % / 0.03 %, FP16 deviations 0.04 % / 0.05 %, BF16 deviations 0.9 % /
+    0.6 %)."""
+    from paper_2102_09512_gb300 import studies
+    r = studies.precision_study(n=128, steps=2000, every=20)
+    for store in ("f32", "f16dev", "bf16dev"):
+        e = r[store]
+        assert e["physical_to"] == 2000, (store, e["physical_to"])
+        assert e["K_drift"] <= 0.01 and e["theta_drift"] <= 0.01, (store, e["K_drift"], e["theta_drift"])
