@@ -147,3 +147,12 @@ def test_wait_timeout_injection_arguments(L):
         L.elbm_inject_wait_timeout(h, 2)
     assert ei.value.code == L.ELBM_ERR_ARG
     L.elbm_destroy(h)
+
+
+def test_grid_size_limit(L):
+    """Node indices are 32-bit: N = 2^31 nodes is the largest grid a handle accepts."""
+    h = L.elbm_create(L.make_params(3, 2048, 1024, 1024, store="f16dev"))
+    L.elbm_destroy(h)
+    with pytest.raises(L.ElbmError) as ei:
+        L.elbm_create(L.make_params(3, 2048, 1024, 1025, store="f16dev"))
+    assert ei.value.code == L.ELBM_ERR_UNSUPPORTED

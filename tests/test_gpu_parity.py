@@ -506,3 +506,27 @@ def test_tma_wait_timeout_is_reported_and_recoverable(E):
     ref = oracle_fields(("tma-timeout",), c, 10)
     assert_parity(g.fields(), ref, TOL["f32"])
     g.close()
+
+
+DEGENERATE = {
+    # one and two planes in z (the pulled planes z - 1 and z + 1 are the plane itself or
+    # the other one), one row in y, and zero-gradient faces on a single plane
+    "nz1": lambda: C.random_smooth(3, 40, 12, 1, seed=91, mu0=0.01, du=0.05, u0=U0_3D),
+    "nz2": lambda: C.random_smooth(3, 40, 12, 2, seed=92, mu0=0.01, du=0.05, u0=U0_3D),
+    "ny1": lambda: C.random_smooth(3, 40, 1, 7, seed=93, mu0=0.01, du=0.05, u0=U0_3D),
+    "nz1-zerograd": lambda: C.random_smooth(3, 36, 9, 1, seed=94, mu0=0.01, du=0.05, u0=U0_3D,
+                                            bc=(1, 1, 1, 1, 1, 1)),
+    "2d-ny1": lambda: C.random_smooth(2, 40, 1, 1, seed=95, mu0=0.01, du=0.05, u0=U0_2D),
+}
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+@pytest.mark.parametrize("case", list(DEGENERATE))
+def test_degenerate_grids(E, case, store):
+    """Degenerate extents against the oracle in every schedule that applies."""
+    c = DEGENERATE[case]()
+    steps = 30
+    ref = oracle_fields(("degenerate", case), c, steps)
+    kernels = [0, 1] if c.D == 2 else ([0, 1, 2, 3] if store == "f32" else [0, 1, 2])
+    for kernel in kernels:
+        assert_parity(gpu_fields(E, c, steps, store, kernel), ref, TOL[store], (case, store, kernel))
