@@ -163,14 +163,14 @@ def aggregate_rate(units_per_rank, ws, ms_max):
     return ws * units_per_rank / (ms_max * 1e-3)
 
 
-def cpu_oracle_sample(min_seconds=10.0, max_seconds=30.0):
-    """The FP64 oracle on the host cores on a 32^3 box of the same generator; returns
-    (GLUPS, threads, description)."""
+def cpu_oracle_sample(min_seconds=10.0, max_seconds=30.0, threads=None):
+    """The FP64 oracle on the host cores (all of them by default) on a 32^3 box of the
+    same generator; returns (GLUPS, threads, description)."""
     import oracle as O
     from paper_2102_09512_gb300 import cases as C
 
     O.build()
-    threads = O.set_threads(os.cpu_count() or 1)
+    threads = O.set_threads(threads or os.cpu_count() or 1)
     n = 32
     c = C.hit(n)
     p = O.Params(D=3, nx=n, ny=n, nz=n, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0, mu_exp=c.mu_exp, bc=c.bc)
@@ -424,7 +424,9 @@ def main():
     cpu = None
     if not args.no_cpu_baseline:
         v, cores, sample = cpu_oracle_sample()
-        cpu = {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle", "sample": sample}
+        v1, _, sample1 = cpu_oracle_sample(min_seconds=5.0, threads=1)
+        cpu = {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle", "sample": sample,
+               "single_thread": {"value": v1, "sample": sample1}}
 
     kernel_key = f"fused3d_{head}_{n_side}" if args.kernel == "fused" else f"{args.kernel}_{head}_{n_side}"
     traffic = _ncu_traffic(kernel_key)
