@@ -155,8 +155,9 @@ int elbm_conservation(elbm_handle *h, double out[5]);
 
 /* The same totals accumulated inside the last step's kernel from the populations
  * it pulled (the state that step produced; the collision conserves the totals).
- * FP64 stores: FP64 throughout; other stores: compensated sums in the arithmetic
- * type per thread, FP64 across threads.  Synchronises. */
+ * FP64 stores: FP64 throughout; other stores: FP32 sums per thread (over the planes a
+ * thread updates) and per warp, FP64 across warps and CTAs (relative rounding of order
+ * 1e-7, below that of the FP32 node values).  Synchronises. */
 int elbm_step_totals(elbm_handle *h, double out[5]);
 
 /* Turbulence statistics of the current state (paper Sec. III.D), volume averages

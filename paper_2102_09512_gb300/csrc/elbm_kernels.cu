@@ -204,6 +204,37 @@ __device__ __forceinline__ void block_sum5(double v[5], double* __restrict__ out
     }
 }
 
+// The same sum for kernels that reduce once per small tile: the sum within each warp runs
+// in the arithmetic type T (an FP64 shuffle tree per 256-node tile costs more than the
+// tile's whole update on GB300's narrow FP64 pipe), the sum of the warp partials in FP64.
+// With T = double it is block_sum5.  An FP32 warp partial of 32 node values carries a
+// relative rounding error of about 1e-7, below the rounding of the FP32 values summed.
+template <typename T>
+__device__ __forceinline__ void block_sum5_warp(T v[5], double* __restrict__ out) {
+    if constexpr (sizeof(T) == 8) {
+        block_sum5(v, out);
+    } else {
+        __shared__ double red[32][5];
+        const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+        const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+        const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) red[warp][k] = (double)v[k];
+        __syncthreads();
+        if (tid < 5) {
+            const int nw = (nthreads + 31) >> 5;
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += red[w][tid];
+            out[tid] = t;
+        }
+    }
+}
+
 __device__ __forceinline__ void flag_if(bool bad, int* __restrict__ status) {
     // every thread of the warp reaches this call
     const unsigned any = __ballot_sync(0xffffffffu, bad);
@@ -416,7 +447,7 @@ __global__ void collide_kernel(const __grid_constant__ KParams p, const P* __res
                                P* __restrict__ dst, const R* __restrict__ qf,
                                double* __restrict__ partials, int* __restrict__ status) {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double tot[5] = {0, 0, 0, 0, 0};
+    R tot[5] = {0, 0, 0, 0, 0};
     bool bad = false;
     if (n < p.N) {
         const int x = (int)(n % p.nx);
@@ -448,15 +479,12 @@ __global__ void collide_kernel(const __grid_constant__ KParams p, const P* __res
             Dz = dQ(p.deriv, m.uz, qf[2 * N + node_index(p, x, y, zm)], qf[2 * N + n],
                     qf[2 * N + node_index(p, x, y, zp)]);
         }
-        R v[5];
-        node_totals(m, m.rE, v);
-#pragma unroll
-        for (int k = 0; k < 5; ++k) tot[k] = (double)v[k];
+        node_totals(m, m.rE, tot);
         collide<kD, R, DEV>(f, g, m, Dx, Dy, Dz, p);
         store_node(p, dst, n, f, g);
     }
     flag_if(bad, status);
-    block_sum5(tot, partials + 5 * blockIdx.x);
+    block_sum5_warp(tot, partials + 5 * blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -543,21 +571,18 @@ __device__ __forceinline__ void fused2d_tile(const KParams& p, const P* __restri
     }
     __syncthreads();
 
-    double tot[5] = {0, 0, 0, 0, 0};
+    R tot[5] = {0, 0, 0, 0, 0};
     bool bad = false;
     if (active) {
         bad = nonphysical(m);
         const R Dx = dQ(p.deriv, m.ux, qx[ty][tx], qx[ty][tx + 1], qx[ty][tx + 2]);
         const R Dy = dQ(p.deriv, m.uy, qy[ty][tx], qy[ty + 1][tx], qy[ty + 2][tx]);
-        R v[5];
-        node_totals(m, m.rE, v);
-#pragma unroll
-        for (int k = 0; k < 5; ++k) tot[k] = (double)v[k];
+        if (partial) node_totals(m, m.rE, tot);
         collide<kD, R, DEV, CAL>(f, g, m, Dx, Dy, R(0), p);
         store_node(p, dst, node_index(p, x, y, 0), f, g);
     }
     flag_if(bad, status);
-    if (partial) block_sum5(tot, partial);
+    if (partial) block_sum5_warp(tot, partial);
     __syncthreads();   // the shared arrays are reused by the next tile of a persistent CTA
 }
 
@@ -797,10 +822,10 @@ fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPla
     }
     cp_async_wait_all();
     flag_if(bad, status);
-    double tot[5];
+    R tot[5];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) tot[k] = (double)acc.s[k] - (double)acc.c[k];
-    block_sum5(tot, partials + 5 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
+    for (int k = 0; k < 5; ++k) tot[k] = acc.s[k] - acc.c[k];
+    block_sum5_warp(tot, partials + 5 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
 }
 
 // ---------------------------------------------------------------------------
@@ -1077,10 +1102,10 @@ fused3d_tma_kernel(const __grid_constant__ KParams p, const __grid_constant__ Di
     }
     cp_async_wait_all();
     flag_if(bad, status);
-    double tot[5];
+    R tot[5];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) tot[k] = (double)acc.s[k] - (double)acc.c[k];
-    block_sum5(tot, partials + 5 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
+    for (int k = 0; k < 5; ++k) tot[k] = acc.s[k] - acc.c[k];
+    block_sum5_warp(tot, partials + 5 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
 }
 
 // D3Q27 without plane buffers: for plane z it computes Q~ of plane z+1 (tile + halo)
@@ -1161,10 +1186,10 @@ fused3d_reread_kernel(const __grid_constant__ KParams p, const P* __restrict__ s
         qz_cur = qz_next;
     }
     flag_if(bad, status);
-    double tot[5];
+    R tot[5];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) tot[k] = (double)acc.s[k] - (double)acc.c[k];
-    block_sum5(tot, partials + 5 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
+    for (int k = 0; k < 5; ++k) tot[k] = acc.s[k] - acc.c[k];
+    block_sum5_warp(tot, partials + 5 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
 }
 
 // ---------------------------------------------------------------------------

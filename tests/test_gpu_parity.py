@@ -530,3 +530,19 @@ def test_degenerate_grids(E, case, store):
     kernels = [0, 1] if c.D == 2 else ([0, 1, 2, 3] if store == "f32" else [0, 1, 2])
     for kernel in kernels:
         assert_parity(gpu_fields(E, c, steps, store, kernel), ref, TOL[store], (case, store, kernel))
+
+
+@pytest.mark.parametrize("D,store,kernel", [(2, "f32", 0), (2, "f32", 1), (2, "f16dev", 0), (3, "f32", 1),
+                                            (3, "f16dev", 1)])
+def test_step_totals_of_the_fp32_arithmetic_paths(E, D, store, kernel):
+    """The step totals of the kernels that sum each warp's node values in FP32 before
+    the FP64 sum over warps equal the FP64 totals of the state they produced, to the
+    rounding of the FP32 node values."""
+    c = C.random_smooth(D, 45, 23, 9 if D == 3 else 1, seed=97, mu0=0.01)
+    g = E.Solver.from_case(c, store=store)
+    g.set_kernel(kernel)
+    g.step(3)
+    t = g.step_totals()
+    ref = g.conservation()
+    assert np.allclose(t, ref, rtol=2e-6, atol=2e-6 * abs(ref[0])), (t, ref)
+    g.close()
