@@ -15,7 +15,7 @@ every rank runs an independent replica of the workload (the path needs no
 exchange between replicas; weak scaling).
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload (a 32^3 box of the same generator) and prints the same
+sample of the same workload (a 64^3 box of the same generator) and prints the same
 JSON line with ``"impl": "reference"``.
 """
 from __future__ import annotations
@@ -163,17 +163,20 @@ def aggregate_rate(units_per_rank, ws, ms_max):
     return ws * units_per_rank / (ms_max * 1e-3)
 
 
-def cpu_oracle_sample(min_seconds=10.0, max_seconds=30.0, threads=None):
-    """The FP64 oracle on the host cores (all of them by default) on a 32^3 box of the
-    same generator; returns (GLUPS, threads, description)."""
+CPU_N = 64   # side of the decaying-turbulence box the oracle is timed on
+
+
+def cpu_oracle_sample(min_seconds=10.0, max_seconds=30.0, threads=None, case=None):
+    """The FP64 oracle on the host cores (all of them by default) on a CPU_N^3 box of the
+    same generator, or on `case`; returns (GLUPS, threads, description)."""
     import oracle as O
     from paper_2102_09512_gb300 import cases as C
 
     O.build()
     threads = O.set_threads(threads or os.cpu_count() or 1)
-    n = 32
-    c = C.hit(n)
-    p = O.Params(D=3, nx=n, ny=n, nz=n, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0, mu_exp=c.mu_exp, bc=c.bc)
+    c = case if case is not None else C.hit(CPU_N)
+    p = O.Params(D=c.D, nx=c.nx, ny=c.ny, nz=c.nz, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0, mu_exp=c.mu_exp,
+                 bc=c.bc)
     s = O.init(p, c.rho, c.u, c.T)
     O.step(s, 1)
     steps = 0
@@ -184,8 +187,10 @@ def cpu_oracle_sample(min_seconds=10.0, max_seconds=30.0, threads=None):
         el = time.perf_counter() - t0
         if el >= min_seconds or el >= max_seconds:
             break
-    glups = n ** 3 * steps / el / 1e9
-    return glups, threads, f"D3Q27 32^3 box of the same turbulence generator, {steps} steps, {el:.1f} s"
+    glups = c.N * steps / el / 1e9
+    what = (f"D3Q27 {CPU_N}^3 box of the same turbulence generator" if case is None
+            else f"D2Q9 {c.nx} x {c.ny} {c.name}")
+    return glups, threads, f"{what}, {steps} steps, {el:.1f} s"
 
 
 def run_reference(args):
@@ -197,7 +202,7 @@ def run_reference(args):
     from paper_2102_09512_gb300 import cases as C
     O.build()
     threads = O.set_threads(os.cpu_count() or 1)
-    n = 32
+    n = CPU_N
     c = C.hit(n)
     p = O.Params(D=3, nx=n, ny=n, nz=n, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0, mu_exp=c.mu_exp, bc=c.bc)
     s = O.init(p, c.rho, c.u, c.T)
@@ -213,9 +218,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "32^3 box, same generator"},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{n}^3 box, same generator"},
         "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": threads, "kind": "oracle",
-                         "sample": f"D3Q27 32^3 box of the same generator, {args.steps} steps"},
+                         "sample": f"D3Q27 {n}^3 box of the same generator, {args.steps} steps"},
         "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -423,10 +428,13 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline:
+        from paper_2102_09512_gb300 import cases as C
         v, cores, sample = cpu_oracle_sample()
         v1, _, sample1 = cpu_oracle_sample(min_seconds=5.0, threads=1)
+        v2, _, sample2 = cpu_oracle_sample(min_seconds=5.0, case=C.shock_vortex(nx=1024, ny=1024, r_v=32.0, Ma_s=1.2))
         cpu = {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle", "sample": sample,
-               "single_thread": {"value": v1, "sample": sample1}}
+               "single_thread": {"value": v1, "sample": sample1},
+               "d2q9_shock_vortex": {"value": v2, "cores": cores, "sample": sample2}}
 
     kernel_key = f"fused3d_{head}_{n_side}" if args.kernel == "fused" else f"{args.kernel}_{head}_{n_side}"
     traffic = _ncu_traffic(kernel_key)
