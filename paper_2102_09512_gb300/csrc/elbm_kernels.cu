@@ -524,7 +524,7 @@ __device__ __forceinline__ bool halo_node(const KParams& p, int h, int x0, int y
 // collides and stores.  One launch per step, no intermediate field in HBM.  The tile
 // body is shared by the per-lattice kernel and the persistent ensemble kernel;
 // `partial` (may be null) receives the tile's totals.
-template <int TY, bool CAL>
+template <int TY, bool CAL, bool ONE_WAIT>
 __device__ __forceinline__ void fused2d_tile(const KParams& p, const P* __restrict__ src, P* __restrict__ dst,
                                              int bx, int by, double* __restrict__ partial,
                                              int* __restrict__ status) {
@@ -536,37 +536,66 @@ __device__ __forceinline__ void fused2d_tile(const KParams& p, const P* __restri
     const bool active = x < p.nx && y < p.ny;
     const int xl = min(x0 + TX, p.nx) - 1 - x0, yl = min(y0 + TY, p.ny) - 1 - y0;
 
+    // ONE_WAIT: both gathers (the node's and its halo node's pairs) are issued before any
+    // arithmetic, so the tile waits for memory once; the persistent ensemble kernel keeps
+    // the node's gather and moments first, which needs fewer registers (64, no spills)
+    const int h = tx + TX * ty;
+    int hx = 0, hy = 0, sx = 0, sy = 0, axis = 0;
+    const bool hv = h < 2 * TX + 2 * TY && halo_node<TY>(p, h, x0, y0, xl, yl, hx, hy, sx, sy, axis);
+    // the unmapped halo coordinate is (x0 + sx - 1, y0 + sy) for columns and (x0 + sx, y0 + sy - 1)
+    // for rows; beyond a fixed face the halo's Q~ is the fixed state's
+    const bool hfixed = hv && p.has_fixed &&
+                        (axis == 1 ? beyond_fixed(p, 1, y0 + sy - 1, p.ny) : beyond_fixed(p, 0, x0 + sx - 1, p.nx));
     R f[Q], g[Q];
     Moments<R> m;
-    if (active) {
-        PullRows r;
-        pull_rows(p, x, y, 0, r);
-        gather(p, src, r, f, g);
-        node_moments<kD, R, true, DEV, CAL>(f, g, p, m);
-        qx[ty][tx + 1] = anomaly(m.rho, m.ux, m.T);
-        qy[ty + 1][tx] = anomaly(m.rho, m.uy, m.T);
-    }
-    {
-        int hx, hy, sx, sy, axis;
-        const int h = tx + TX * ty;
-        if (h < 2 * TX + 2 * TY && halo_node<TY>(p, h, x0, y0, xl, yl, hx, hy, sx, sy, axis)) {
+    auto halo_q = [&](const R* hf, const R* hg) {
+        Moments<R> hm;
+        node_moments<kD, R, false, DEV, CAL>(hf, hg, p, hm);
+        return anomaly(hm.rho, axis == 1 ? hm.uy : hm.ux, hm.T);
+    };
+    auto store_halo_q = [&](R q) {
+        if (axis == 1) qy[sy][sx] = q;
+        else qx[sy][sx] = q;
+    };
+    if constexpr (ONE_WAIT) {
+        R hf[Q], hg[Q];
+        if (active) {
+            PullRows r;
+            pull_rows(p, x, y, 0, r);
+            gather(p, src, r, f, g);
+        }
+        if (hv && !hfixed) {
+            PullRows r;
+            pull_rows(p, hx, hy, 0, r);
+            gather(p, src, r, hf, hg);
+        }
+        if (active) {
+            node_moments<kD, R, true, DEV, CAL>(f, g, p, m);
+            qx[ty][tx + 1] = anomaly(m.rho, m.ux, m.T);
+            qy[ty + 1][tx] = anomaly(m.rho, m.uy, m.T);
+        }
+        if (hv) store_halo_q(hfixed ? fixed_Q(p, axis) : halo_q(hf, hg));
+    } else {
+        if (active) {
+            PullRows r;
+            pull_rows(p, x, y, 0, r);
+            gather(p, src, r, f, g);
+            node_moments<kD, R, true, DEV, CAL>(f, g, p, m);
+            qx[ty][tx + 1] = anomaly(m.rho, m.ux, m.T);
+            qy[ty + 1][tx] = anomaly(m.rho, m.uy, m.T);
+        }
+        if (hv) {
             R q;
-            // the unmapped halo coordinate is (x0 + sx - 1, y0 + sy) for columns and
-            // (x0 + sx, y0 + sy - 1) for rows
-            if (p.has_fixed && (axis == 1 ? beyond_fixed(p, 1, y0 + sy - 1, p.ny)
-                                          : beyond_fixed(p, 0, x0 + sx - 1, p.nx))) {
+            if (hfixed) {
                 q = fixed_Q(p, axis);
             } else {
                 PullRows r;
                 pull_rows(p, hx, hy, 0, r);
                 R hf[Q], hg[Q];
                 gather(p, src, r, hf, hg);
-                Moments<R> hm;
-                node_moments<kD, R, false, DEV, CAL>(hf, hg, p, hm);
-                q = anomaly(hm.rho, axis == 1 ? hm.uy : hm.ux, hm.T);
+                q = halo_q(hf, hg);
             }
-            if (axis == 1) qy[sy][sx] = q;
-            else qx[sy][sx] = q;
+            store_halo_q(q);
         }
     }
     __syncthreads();
@@ -590,7 +619,7 @@ template <int TY, bool CAL>
 __global__ void __launch_bounds__(TX * TY)
 fused2d_kernel(const __grid_constant__ KParams p, const P* __restrict__ src, P* __restrict__ dst,
                double* __restrict__ partials, int* __restrict__ status) {
-    fused2d_tile<TY, CAL>(p, src, dst, blockIdx.x, blockIdx.y, partials + 5 * (blockIdx.x + gridDim.x * blockIdx.y),
+    fused2d_tile<TY, CAL, true>(p, src, dst, blockIdx.x, blockIdx.y, partials + 5 * (blockIdx.x + gridDim.x * blockIdx.y),
                      status);
 }
 
@@ -613,7 +642,7 @@ ensemble2d_kernel(const EnsembleArgs a, const P* __restrict__ src, P* __restrict
         const int local = t - s_start[k];
         const int bx = local % s_tx[k], by = local / s_tx[k];
         const long long off = a.offset[k];
-        fused2d_tile<TY, CAL>(a.params[k], src + off, dst + off, bx, by, nullptr, status);
+        fused2d_tile<TY, CAL, false>(a.params[k], src + off, dst + off, bx, by, nullptr, status);
     }
 }
 
