@@ -748,10 +748,14 @@ fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPla
     // tile nodes: halo nodes contribute Q~ alone)
     auto slot_moments = [&](int sb, int slot, Moments<R>& m, auto full) {
         const P* bb = buf + (size_t)sb * Q * NS + slot;
-        R f[Q], g[Q];
+        if constexpr (DEV) {   // sums straight from the stored pairs
+            node_moments_stored<kD, kST, decltype(full)::value, CAL>([&](int i) { return bb[i * NS]; }, p, m);
+        } else {
+            R f[Q], g[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], f[i], g[i]);
-        node_moments<kD, R, decltype(full)::value, DEV, CAL>(f, g, p, m);
+            for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], f[i], g[i]);
+            node_moments<kD, R, decltype(full)::value, DEV, CAL>(f, g, p, m);
+        }
     };
     using Full = std::true_type;
     using Lite = std::false_type;
@@ -1028,10 +1032,15 @@ fused3d_tma_kernel(const __grid_constant__ KParams p, const __grid_constant__ Di
     };
     auto slot_moments = [&](int sb, int slot, Moments<R>& m, auto full) {
         const P* bb = buf + (size_t)sb * Q * BOXP + slot;
-        R f[Q], g[Q];
+        if constexpr (DEV) {   // sums straight from the stored pairs
+            node_moments_stored<kD, kST, decltype(full)::value, CAL>([&](int i) { return bb[i * BOXP - cx_of(i)]; },
+                                                                       p, m);
+        } else {
+            R f[Q], g[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) Cd::dec(bb[i * BOXP - cx_of(i)], f[i], g[i]);
-        node_moments<kD, R, decltype(full)::value, DEV, CAL>(f, g, p, m);
+            for (int i = 0; i < Q; ++i) Cd::dec(bb[i * BOXP - cx_of(i)], f[i], g[i]);
+            node_moments<kD, R, decltype(full)::value, DEV, CAL>(f, g, p, m);
+        }
     };
     using Full = std::true_type;
     using Lite = std::false_type;

@@ -80,6 +80,31 @@ template <> struct Codec<ST_F32> {
     __device__ __forceinline__ static void dec(P v, R& f, R& g) { f = v.x; g = v.y; }
     __device__ __forceinline__ static P enc(R f, R g) { return make_float2(f, g); }
 };
+// Mixed-precision add and subtract (sm_100 and later): a 16-bit operand a, exact in
+// FP32, combined with an FP32 operand c and rounded once to FP32 — the same result as
+// converting a first, in one instruction.  The deviation stores use them to sum moments
+// straight from the stored pairs.
+__device__ __forceinline__ float mixed_add_f16(unsigned short a, float c) {
+    float d;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float mixed_sub_f16(unsigned short a, float c) {
+    float d;
+    asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float mixed_add_bf16(unsigned short a, float c) {
+    float d;
+    asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float mixed_sub_bf16(unsigned short a, float c) {
+    float d;
+    asm("sub.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(c));
+    return d;
+}
+
 template <> struct Codec<ST_F16DEV> {
     using P = __half2;
     using R = float;
@@ -90,6 +115,14 @@ template <> struct Codec<ST_F16DEV> {
         g = d.y;
     }
     __device__ __forceinline__ static P enc(R f, R g) { return __floats2half2_rn(f, g); }
+    // f or g component of a stored pair: to FP32, plus / minus an FP32 value
+    __device__ __forceinline__ static float f32(P v, int k) { return __half2float(k ? __high2half(v) : __low2half(v)); }
+    __device__ __forceinline__ static float add(P v, int k, float c) {
+        return mixed_add_f16(__half_as_ushort(k ? __high2half(v) : __low2half(v)), c);
+    }
+    __device__ __forceinline__ static float sub(P v, int k, float c) {
+        return mixed_sub_f16(__half_as_ushort(k ? __high2half(v) : __low2half(v)), c);
+    }
 };
 template <> struct Codec<ST_BF16DEV> {
     using P = __nv_bfloat162;
@@ -101,6 +134,15 @@ template <> struct Codec<ST_BF16DEV> {
         g = d.y;
     }
     __device__ __forceinline__ static P enc(R f, R g) { return __floats2bfloat162_rn(f, g); }
+    __device__ __forceinline__ static float f32(P v, int k) {
+        return __bfloat162float(k ? __high2bfloat16(v) : __low2bfloat16(v));
+    }
+    __device__ __forceinline__ static float add(P v, int k, float c) {
+        return mixed_add_bf16(__bfloat16_as_ushort(k ? __high2bfloat16(v) : __low2bfloat16(v)), c);
+    }
+    __device__ __forceinline__ static float sub(P v, int k, float c) {
+        return mixed_sub_bf16(__bfloat16_as_ushort(k ? __high2bfloat16(v) : __low2bfloat16(v)), c);
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -246,6 +288,68 @@ __device__ __forceinline__ void finish_moments(R rho, R jx, R jy, R jz, R rE, co
     m.uz = jz * inv;
     const R u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
     m.T = T_of_U<R, CAL>(rE * inv - R(0.5) * u2, p);
+}
+
+// The same moments straight from the stored pairs of a deviation store: pair(i) returns
+// the stored (f_i, g_i) of direction i.  Per (c_y, c_z) row one component is converted and
+// the other two enter through mixed-precision adds (hi + lo, hi - lo, mid + (hi + lo));
+// the energy is the sum of the nine row sums of g.  The rounding is that of f_moments
+// and g_energy on the converted values, up to the order of the energy sum.
+template <int D, int ST, bool FULL, bool CAL = true, class Pair>
+__device__ __forceinline__ void node_moments_stored(Pair pair, const KParams& p, Moments<float>& m) {
+    using Cd = Codec<ST>;
+    using R = float;
+    constexpr int NC = Lat<D>::NC;
+    R t[3][3], d[3][3], e[3][3], gr[3][3];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int i0 = 3 * b + 9 * c;
+            const auto lo = pair(i0), mid = pair(i0 + 1), hi = pair(i0 + 2);
+            const R lo32 = Cd::f32(lo, 0);
+            e[b][c] = Cd::add(hi, 0, lo32);
+            d[b][c] = Cd::sub(hi, 0, lo32);
+            t[b][c] = Cd::add(mid, 0, e[b][c]);
+            gr[b][c] = Cd::add(hi, 1, Cd::add(mid, 1, Cd::f32(lo, 1)));
+        }
+    R tb[3], db[3], eb[3], gb[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        tb[b] = t[b][0];
+        db[b] = d[b][0];
+        eb[b] = e[b][0];
+        gb[b] = gr[b][0];
+        if (D == 3) {
+            tb[b] = (t[b][0] + t[b][2]) + t[b][1];
+            db[b] = (d[b][0] + d[b][2]) + d[b][1];
+            eb[b] = (e[b][0] + e[b][2]) + e[b][1];
+            gb[b] = (gr[b][0] + gr[b][2]) + gr[b][1];
+        }
+    }
+    R rho = (tb[0] + tb[2]) + tb[1];
+    const R jx = (db[0] + db[2]) + db[1];
+    const R jy = tb[2] - tb[0];
+    R jz = 0;
+    R Pxx = (eb[0] + eb[2]) + eb[1], Pyy = tb[2] + tb[0], Pxy = db[2] - db[0];
+    R Pzz = 0, Pxz = 0, Pyz = 0;
+    if (D == 3) {
+        const R tzh = (t[0][2] + t[2][2]) + t[1][2], tzl = (t[0][0] + t[2][0]) + t[1][0];
+        const R dzh = (d[0][2] + d[2][2]) + d[1][2], dzl = (d[0][0] + d[2][0]) + d[1][0];
+        jz = tzh - tzl;
+        Pzz = tzh + tzl;
+        Pxz = dzh - dzl;
+        Pyz = (t[2][2] - t[0][2]) - (t[2][0] - t[0][0]);
+    }
+    rho += R(p.rest_rho);
+    const R rE = ((gb[0] + gb[2]) + gb[1]) + R(p.rest_E);
+    finish_moments<R, CAL>(rho, jx, jy, jz, rE, p, m);
+    if (FULL) {
+        m.Pxx = Pxx + R(p.rest_Pxx);
+        m.Pyy = Pyy + R(p.rest_Pyy);
+        m.Pzz = Pzz + R(p.rest_Pzz);
+        m.Pxy = Pxy; m.Pxz = Pxz; m.Pyz = Pyz;
+    }
 }
 
 // All moments of one node: f_moments, g_energy, finish_moments.
