@@ -954,10 +954,10 @@ struct Tma {
 //   plane z and store.
 // A wait that gives up (about one second) latches kStatusTimeoutBit, and the CTA stops
 // after waiting, again bounded, for the copies it still has in flight.
-// A selectable schedule: at 256^3 it matches fused3d_kernel in FP32 and runs 2 % slower
-// with FP16 pairs.  It executes 6 % fewer instructions and waits far less at the plane
-// barrier, but the boxes carry 11-19 % more pairs than the pulls use (corners, and the
-// columns that keep the box 16-byte aligned) and the kernel draws more DRAM reads.
+// A selectable schedule: at 256^3 it runs level with fused3d_kernel (within 1 %).  It
+// executes fewer instructions and waits far less at the plane barrier, but the boxes
+// carry 11-19 % more pairs than the pulls use (corners, and the columns that keep the
+// box 16-byte aligned) and the kernel draws 12-25 % more DRAM reads.
 template <int TY, int MINB, int DD, bool CAL>
 __global__ void __launch_bounds__(TX * TY, MINB)
 fused3d_tma_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPlanes pl,
