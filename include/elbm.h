@@ -30,7 +30,8 @@
  *  - Errors: every function returns an elbm_status (0 = ELBM_OK).  Argument errors
  *    are reported synchronously.  Conditions found on the device (non-finite
  *    moments, rho <= 0 or T <= 0) are latched in the auxiliary buffer and reported
- *    by the next synchronising call as ELBM_ERR_NONPHYSICAL.
+ *    by the next synchronising call as ELBM_ERR_NONPHYSICAL; a bounded device wait
+ *    that gave up (ELBM_KERNEL_FUSED_TMA) is reported as ELBM_ERR_TIMEOUT.
  *  - A handle is not thread-safe.
  */
 #ifndef ELBM_H

@@ -275,7 +275,7 @@ def _center_after_one_step(c, x, y, z):
 @pytest.mark.parametrize("store,tol,drift", [("f32", 2e-6, 1e-6), ("f16dev", 2e-4, 1e-5)])
 def test_full_size_256_sampled_nodes(E, store, tol, drift, kernel):
     """At the bench's full size (D3Q27, 256^3, decaying-turbulence field; the fused
-    cp.async kernel the bench times, and the bulk-copy one) sampled nodes after one
+    cp.async kernel the bench times, and the tensor-copy one) sampled nodes after one
     step equal the oracle's one-by-one values, and the totals are conserved over 5
     steps (FP16: up to the storage rounding, 2^-11 of deviations that are a few
     percent of the populations)."""
