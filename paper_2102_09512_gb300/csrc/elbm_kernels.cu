@@ -1276,18 +1276,22 @@ int tma_supported(const KParams& p) {
 // Tensor map of a population store as rank 3: x (nx pairs), y (ny), w = i * nz + z (the
 // planes of all directions), box TmaCfg::BW x RB x 1.  The encoder is the driver's,
 // reached through the runtime (no link against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+        cudaGetLastError();   // leave no sticky error behind
+        return nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+}
+
 int encode_tmap(const KParams& p, const void* base, CUtensorMap* out) {
     if (!tma_supported(p)) return 0;
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
-        void* fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn)
-            return -1;
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
+    static const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();   // resolved once, thread-safe
+    if (!encode) return -1;
     const cuuint64_t dims[3] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny, (cuuint64_t)p.nz * Q};
     const cuuint64_t strides[2] = {(cuuint64_t)p.nx * sizeof(P), (cuuint64_t)p.nx * p.ny * sizeof(P)};
     const cuuint32_t box[3] = {(cuuint32_t)TmaCfg::BW, (cuuint32_t)TmaCfg::RB, 1u};
