@@ -246,11 +246,11 @@ def time_store(E, torch, case, store, steps, warmup, stream, kernel=0):
         e1.record(stream)
     e1.synchronize()
     rc = E.elbm_sync(g.h)
-    if rc != 0:
-        g.close()
-        raise E.ElbmError(rc, f"timed steps {warmup + 1}..{warmup + steps}")
     ms = e0.elapsed_time(e1) / steps
-    return ms, g.launches - l0, g
+    # A state that left the stable range inside the timed window does not change the work
+    # of a step (the same instructions and bytes per node); the timing stands and the
+    # caller reports the status beside it.
+    return ms, g.launches - l0, g, rc
 
 
 def time_e2e(E, torch, case, store, steps, stream):
@@ -271,47 +271,78 @@ def time_e2e(E, torch, case, store, steps, stream):
     g.step(2)
     g.step_totals()
     torch.cuda.synchronize()
+    tot = np.zeros(5)
+    worst = 0
     t0 = time.perf_counter()
     E._check(E.elbm_set_fields(g.h, rho, u, T), "elbm_set_fields")
     for _ in range(steps):
         g.step(1)
-        g.step_totals()
-    E._check(E.elbm_get_fields(g.h, out[0], out[1], out[2]), "elbm_get_fields")
+        # the step's totals come back every step (a non-physical status is kept, not raised:
+        # the step did the same work)
+        rc = E.lib().elbm_step_totals(g.h, tot.ctypes.data_as(E._dp))
+        if rc not in (0, E.ELBM_ERR_NONPHYSICAL):
+            E._check(rc, "elbm_step_totals")
+        worst = worst or rc
+    rc = E.elbm_get_fields(g.h, out[0], out[1], out[2])
+    if rc not in (0, E.ELBM_ERR_NONPHYSICAL):
+        E._check(rc, "elbm_get_fields")
     el = time.perf_counter() - t0
     g.close()
     h2d = 5 * 8 * N / steps
     d2h = (5 * 8 * N) / steps + 5 * 8
-    return 1e3 * el / steps, h2d, d2h
+    return 1e3 * el / steps, h2d, d2h, worst or rc
+
+
+ENSEMBLE_MAX_STEPS = 50   # timed steps per ensemble phase (see ensemble_measure)
 
 
 def ensemble_measure(E, torch, steps, store="f32"):
     """Batched ensemble of 64 uneven D2Q9 instances (Sod tubes and shock-vortex cases,
     sides 256..1024, Ma_s ~ U[1.1, 1.5]): one persistent autotuned launch per step
-    replayed from a CUDA graph, against one launch per instance."""
+    replayed from a CUDA graph, against one launch per instance.  Each mode starts from
+    the initial fields and is timed over at most ENSEMBLE_MAX_STEPS steps after 3 warm-up
+    steps: shock-vortex instances with Ma_s of 1.3 and above leave the scheme's stable
+    range after 150-380 steps (FP32; from Ma_s = 1.41 in FP64 too).  A mode that fails
+    reports its error instead of a rate."""
     from paper_2102_09512_gb300 import cases as C
     specs = C.ensemble(64)
     cases = [C.build_instance(s) for s in specs]
+    k = min(steps, ENSEMBLE_MAX_STEPS)
     ens = E.Ensemble.from_cases(cases, store=store)
-    ty, ctas, grid = ens.tune(trial_steps=3)
-    out = {"instances": len(cases), "nodes": ens.nodes, "store": store,
-           "schedule": {"tile": [32, ty], "ctas_per_sm": ctas, "grid": grid}}
+    out = {"instances": len(cases), "nodes": ens.nodes, "store": store, "timed_steps": k}
+    try:
+        ty, ctas, grid = ens.tune(trial_steps=3)
+    except E.ElbmError as err:
+        ens.close()
+        out["error"] = f"tuning: {err}"
+        return out
+    out["schedule"] = {"tile": [32, ty], "ctas_per_sm": ctas, "grid": grid}
     for name, mode, graph in (("persistent_graph", 0, True), ("per_instance", 1, False)):
-        ens.set_mode(mode, graph)
-        ens.step(3)
-        ens.sync()
-        l0 = ens.launches
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(ens.stream)
-        ens.step(steps)
-        e1.record(ens.stream)
-        e1.synchronize()
-        ens.sync()
-        ms = e0.elapsed_time(e1) / steps
-        out[name] = {"ms_per_step": ms, "glups": ens.nodes / (ms * 1e-3) / 1e9,
-                     "launches_per_step": (ens.launches - l0) / steps}
-    out["speedup_persistent_vs_per_instance"] = out["per_instance"]["ms_per_step"] / out["persistent_graph"]["ms_per_step"]
-    ens.close()
+        if ens is None:
+            ens = E.Ensemble.from_cases(cases, store=store)   # the next mode starts from the initial fields
+            ens.set_schedule(ty, ctas)
+        try:
+            ens.set_mode(mode, graph)
+            ens.step(3)
+            ens.sync()
+            l0 = ens.launches
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(ens.stream)
+            ens.step(k)
+            e1.record(ens.stream)
+            e1.synchronize()
+            ens.sync()
+            ms = e0.elapsed_time(e1) / k
+            out[name] = {"ms_per_step": ms, "glups": ens.nodes / (ms * 1e-3) / 1e9,
+                         "launches_per_step": (ens.launches - l0) / k}
+        except E.ElbmError as err:
+            out[name] = {"error": str(err)}
+        ens.close()
+        ens = None
+    if "glups" in out["persistent_graph"] and "glups" in out["per_instance"]:
+        out["speedup_persistent_vs_per_instance"] = (out["per_instance"]["ms_per_step"] /
+                                                     out["persistent_graph"]["ms_per_step"])
     return out
 
 
@@ -380,7 +411,7 @@ def main():
         if sampler:
             sampler.start()
         try:
-            ms, launches, g = time_store(E, torch, case, store, k, warm, stream, KERNELS[args.kernel])
+            ms, launches, g, rc = time_store(E, torch, case, store, k, warm, stream, KERNELS[args.kernel])
         except E.ElbmError as err:
             if sampler:
                 sampler.stop()
@@ -393,7 +424,10 @@ def main():
         if sampler:
             clocks = sampler.stop()
         ms = replica_time(ms, ws, "cuda")
-        totals = g.conservation()
+        try:
+            totals = g.conservation()
+        except E.ElbmError:
+            totals = [float("nan")] * 5
         g.close()
         del g
         torch.cuda.empty_cache()
@@ -407,6 +441,8 @@ def main():
                            "hbm_frac": per_gpu_gbs / peak, "bytes_per_update": BYTES_PER_UPDATE[store],
                            "kernel_launches_per_step": launches / k,
                            "mass_total": float(totals[0]), "energy_total": float(totals[4])}
+        if rc != 0:
+            variants[store]["status_after_timed_steps"] = E.elbm_status_str(rc)
         if head is None and "error" not in variants[store]:
             head = store
             launches_head = launches
@@ -418,9 +454,11 @@ def main():
     # end-to-end through the C ABI with host buffers (headline store)
     e2e = None
     if not args.no_e2e:
-        e2e_ms, h2d, d2h = time_e2e(E, torch, case, head, args.steps, stream)
+        e2e_ms, h2d, d2h, e2e_rc = time_e2e(E, torch, case, head, args.steps, stream)
         e2e = {"value": ws * case.N / (e2e_ms * 1e-3) / 1e9, "unit": "GLUPS", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
+        if e2e_rc != 0:
+            e2e["status"] = E.elbm_status_str(e2e_rc)
 
     ens = None
     if not args.no_ensemble:
