@@ -272,13 +272,16 @@ def _center_after_one_step(c, x, y, z):
 
 
 @pytest.mark.parametrize("kernel", [0, 3])
-@pytest.mark.parametrize("store,tol,drift", [("f32", 2e-6, 1e-6), ("f16dev", 2e-4, 1e-5)])
+@pytest.mark.parametrize("store,tol,drift", [("f32", 2e-6, 1e-6), ("f16dev", 2e-4, 1e-5), ("bf16dev", 4e-3, 8e-5)])
 def test_full_size_256_sampled_nodes(E, store, tol, drift, kernel):
     """At the bench's full size (D3Q27, 256^3, decaying-turbulence field; the fused
     cp.async kernel the bench times, and the tensor-copy one) sampled nodes after one
     step equal the oracle's one-by-one values, and the totals are conserved over 5
     steps (FP16: up to the storage rounding, 2^-11 of deviations that are a few
-    percent of the populations)."""
+    percent of the populations).  BF16 keeps 8 significand bits: each stored deviation
+    carries a relative rounding of up to 2^-9 and the deviations of a node sum in
+    magnitude to at most about 2 rho, so rho, T and rho u move by up to about
+    2 * 2^-9 = 3.9e-3 (relative): the bound is 4e-3 for rho and T, 2e-3 for u."""
     c = C.hit(256, seed=20210218)
     g = E.Solver.from_case(c, store=store)
     g.set_kernel(kernel)
@@ -565,3 +568,32 @@ def test_shock_vortex_1024_full_run_fp32_against_fp64(E):
     for a, b in zip(out["f32"], out["f64"]):
         assert np.all(np.isfinite(a))
         assert rel_l2(a, b) <= 5e-4
+
+
+
+@pytest.mark.parametrize("store,tol", [("f32", 2e-6), ("f16dev", 2e-4)])
+def test_full_size_512_sampled_nodes(E, store, tol):
+    """The 512^3 decaying-turbulence grid (134 M nodes, the larger size of the
+    reduced-precision study): sampled nodes after one step of the default fused kernel
+    equal the oracle's one-by-one values."""
+    c = C.hit(512, seed=20210218, dtype=np.float32)
+    g = E.Solver.from_case(c, store=store)
+    g.step(1)
+    import torch
+    n3 = 512 ** 3
+    rho = torch.empty(n3, dtype=torch.float64, device="cuda")
+    u = torch.empty(3 * n3, dtype=torch.float64, device="cuda")
+    T = torch.empty(n3, dtype=torch.float64, device="cuda")
+    g.fields_device(rho, u, T)
+    g.sync()
+    rng = np.random.default_rng(9)
+    pts = rng.integers(0, 512, size=(8, 3))
+    pts[0] = (0, 0, 0)
+    pts[1] = (511, 511, 511)
+    for x, y, z in pts:
+        n = int(x + 512 * (y + 512 * z))
+        r_o, u_o, T_o = _center_after_one_step(c, x, y, z)
+        assert abs(float(rho[n]) - r_o) <= tol * abs(r_o)
+        assert abs(float(T[n]) - T_o) <= tol * abs(T_o)
+        assert max(abs(float(u[a * n3 + n]) - u_o[a]) for a in range(3)) <= tol * 0.5
+    g.close()
