@@ -359,6 +359,48 @@ def test_global_conservation_periodic(D, shape):
     assert np.all(np.abs(c1 - c0) / scale < 2e-14)
 
 
+@pytest.mark.parametrize("D,shape,caloric", [(2, (13, 7, 1), False), (3, (6, 5, 4), False), (3, (5, 4, 3), True)])
+def test_conservation_totals_equal_the_field_sums(D, shape, caloric):
+    """At f = f^eq, g = g^eq (the initial state) the totals of Eqs. density, momentum and
+    energy are the sums of the input fields: sum rho, sum rho u_a and sum rho (U(T) + u^2/2)
+    with U = Cv T for constant Cv = 1/(gamma - 1), or the integral of the cubic Cv(T)
+    (Eq. U).  The reference sums are exactly rounded sums (math.fsum) of the fields, with no
+    oracle call, so a total taken on the wrong axis or from the wrong population fails."""
+    nx, ny, nz = shape
+    c = C.random_smooth(D, nx, ny, nz, seed=17, mu0=0.02, du=0.2, u0=(0.05, -0.1, 0.15))
+    if caloric:
+        c.cv = CV_POLY
+    tot = O.conservation(O.init(params_of(c), c.rho, c.u, c.T))
+    rho, T = c.rho.ravel(), c.T.ravel()
+    u = [c.u[a].ravel() for a in range(D)]
+    U = _U_poly(T) if caloric else T / (c.gamma - 1.0)
+    ke = 0.5 * sum(ua * ua for ua in u)
+    ref = [math.fsum(rho)] + [math.fsum(rho * ua) for ua in u] + [0.0] * (3 - D) + [math.fsum(rho * (U + ke))]
+    scale = [ref[0]] * 4 + [ref[4]]
+    for k in range(5):
+        assert abs(tot[k] - ref[k]) <= 1e-14 * scale[k], (k, tot[k], ref[k])
+
+
+def test_conservation_totals_are_compensated():
+    """One node 1e16 times as dense as the others (1000 nodes, in node order first): every
+    later node's mass is below half an ulp of the running sum, so a plain left-to-right sum
+    returns the heavy node alone (mass short by 999, energy off by about 120).  The
+    compensated sum keeps them; what remains is the per-node rounding of the heavy node's
+    population sums (a few units of its last place)."""
+    nx, ny = 40, 25
+    rho = np.ones((1, ny, nx))
+    rho[0, 0, 0] = 1e16
+    T = np.full((1, ny, nx), 0.15)
+    u = np.zeros((2, 1, ny, nx))
+    u[0] = 0.1
+    p = O.Params(D=2, nx=nx, ny=ny, nz=1, mu0=0.02)
+    tot = O.conservation(O.init(p, rho, u, T))
+    r, U = rho.ravel(), T.ravel() / (1.4 - 1.0)
+    assert abs(tot[0] - math.fsum(r)) <= 16.0
+    assert abs(tot[1] - math.fsum(0.1 * r)) <= 2.0
+    assert abs(tot[4] - math.fsum(r * (U + 0.005))) <= 8.0
+
+
 @pytest.mark.parametrize("D", [2, 3])
 def test_uniform_flow_is_a_fixed_point(D):
     """A uniform state (with flow) initialised at equilibrium stays put: the
@@ -430,9 +472,9 @@ def _track(c, p, field_, nsteps, every):
     return np.array(ts), np.array(amps)
 
 
-def _sound(U0, correction, D=2, T0=0.15, mu=0.01, L=64):
+def _sound(U0, correction, D=2, T0=0.15, mu=0.01, L=64, deriv=0):
     c = C.sound_wave(D=D, L=L, U0=U0, mu=mu, T0=T0, A=1e-5)
-    p = params_of(c, correction=correction)
+    p = params_of(c, correction=correction, deriv=deriv)
     ts, a = _track(c, p, "rho", 1500, 10)
     sel = ts >= 200
     Gam = -np.polyfit(ts[sel], np.log(np.abs(a[sel])), 1)[0]
@@ -452,6 +494,18 @@ def test_sound_speed_and_attenuation(U0):
     and decays at the NSF rate k^2/2 [(4/3 mu + varsigma)/rho + (gamma-1) kappa/(rho Cp)]
     with the model's bulk viscosity (Eq. bulkvisc), at rest and advected."""
     c_meas, c_exp, G, G_nsf = _sound(U0, 1)
+    assert c_meas == pytest.approx(c_exp, rel=2e-3)
+    assert G == pytest.approx(G_nsf, rel=0.02)
+
+
+@pytest.mark.parametrize("U0", [0.0, 0.2])
+def test_sound_attenuation_with_central_derivative(U0):
+    """The second-order central derivative of Q~_aaa (Sec. III.A's comparison scheme)
+    removes the same anomaly as the upwind one: at amplitude 1e-5 the wave runs at
+    sqrt(gamma T) and decays at the NSF rate within the same bounds, at rest and advected.
+    A derivative twice too large or of the wrong sign over- or under-corrects the normal
+    stress and moves the attenuation by more than 100 %."""
+    c_meas, c_exp, G, G_nsf = _sound(U0, 1, deriv=1)
     assert c_meas == pytest.approx(c_exp, rel=2e-3)
     assert G == pytest.approx(G_nsf, rel=0.02)
 
