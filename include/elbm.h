@@ -220,7 +220,9 @@ int elbm_velocity(int lattice, int i, int c[3]);
  * D3Q27 with FP32/FP16/BF16 stores, 0.69 M for FP64, 2.05 M for D2Q9 FP32; larger
  * grids return ELBM_ERR_UNSUPPORTED before anything is launched.
  * The first call on a device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream capture.
+ * with that device current); make that first call before any stream capture.  The
+ * address belongs to the device's context: after a cudaDeviceReset the next call looks
+ * it up again, so make the first call after a reset before any capture as well.
  * Calls no cudaMalloc, cudaFree or other allocating routine.  All calls share the
  * array, so calls whose kernels overlap on the GPU (different streams, or several
  * host threads) race on it; serialise them.  The status word is cleared by each

@@ -170,6 +170,31 @@ inline int fill_kparams(const elbm_params& p, KParams& k, int* D_out) {
     return ELBM_OK;
 }
 
+// Threads per CTA of the one-dimensional launches (initialisation, field extraction, the
+// two passes of the two-pass schedule).  The two-pass step writes one partial vector of
+// step totals per CTA of that grid, so every scratch layout sizes its partials by
+// blocks_1d_of(N).
+constexpr int kThreads1D = 256;
+inline long long blocks_1d_of(long long n) { return (n + kThreads1D - 1) / kThreads1D; }
+
+// Scratch of the allocation-free step (elbm_step_noalloc): status word, per-CTA partials
+// of the two-pass step, Q~ field (D values of the arithmetic type per node); offsets
+// 256-byte aligned.  The static device array that holds it has kNoallocScratchBytes; a
+// grid whose layout needs more is rejected before anything is launched.
+constexpr size_t kNoallocScratchBytes = size_t(16) << 20;
+struct NoallocLayout {
+    size_t status, partials, qfield, bytes;
+};
+inline NoallocLayout noalloc_layout(long long N, int D, size_t real_bytes) {
+    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+    NoallocLayout l;
+    l.status = 0;
+    l.partials = up(sizeof(int));
+    l.qfield = up(l.partials + (size_t)blocks_1d_of(N) * 5 * sizeof(double));
+    l.bytes = up(l.qfield + (size_t)D * (size_t)N * real_bytes);
+    return l;
+}
+
 // Layout of the auxiliary buffer (all offsets 256-byte aligned).
 struct AuxLayout {
     size_t status;      // int32 status word

@@ -1233,7 +1233,7 @@ fused3d_reread_kernel(const __grid_constant__ KParams p, const P* __restrict__ s
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-constexpr int kThreads = 256;
+constexpr int kThreads = kThreads1D;
 constexpr int kTY2 = 8;                  // D2Q9 fused tile 32 x 8
 #ifndef ELBM_TY3
 #define ELBM_TY3 8
@@ -1303,7 +1303,7 @@ int encode_tmap(const KParams& p, const void* base, CUtensorMap* out) {
     return r == CUDA_SUCCESS ? 1 : -1;
 }
 
-inline unsigned blocks_1d(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+inline unsigned blocks_1d(long long n) { return (unsigned)blocks_1d_of(n); }
 
 dim3 fused_grid(const KParams& p) {
     if (kD == 2) return dim3((p.nx + TX - 1) / TX, (p.ny + kTY2 - 1) / kTY2, 1);

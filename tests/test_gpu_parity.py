@@ -119,10 +119,42 @@ def test_d2q9_parity(E, case, store, kernel):
 @pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("case,store", PAIRS)
 def test_d3q27_parity(E, case, store, kernel):
+    """Every store (BF16 included) on small ragged grids over 40 steps; the 100-step
+    window follows in test_d3q27_parity_100_steps."""
     c = CASES_3D[case]()
     steps = 40
     ref = oracle_fields(("3d", case), c, steps)
     assert_parity(gpu_fields(E, c, steps, store, kernel), ref, TOL[store], (case, kernel, store))
+
+
+# 100-step D3Q27 parity on a grid ragged against the 32 x 8 tiles (40 x 27) and long in z
+# (80 planes), marched in the z segments the bench workload uses on 152 SMs (64 planes for
+# the FP32 store, 37 for FP16): several segments, one of them the full-length pipeline.
+LONG_3D = {
+    "periodic": lambda: C.random_smooth(3, 40, 27, 80, seed=121, mu0=0.01, du=0.05, u0=U0_3D),
+    "zerograd": lambda: C.random_smooth(3, 40, 27, 80, seed=122, mu0=0.01, du=0.05, u0=U0_3D,
+                                        bc=(1, 1, 0, 0, 1, 1)),
+    "periodic-zm": lambda: C.random_smooth(3, 40, 27, 80, seed=123, mu0=0.01),
+    "zerograd-zm": lambda: C.random_smooth(3, 40, 27, 80, seed=124, mu0=0.01, bc=(1, 1, 0, 0, 1, 1)),
+}
+LONG_PAIRS = [(case, store) for case in ("periodic", "zerograd") for store in ("f64", "f32", "f16dev")] + \
+             [("periodic-zm", "f64"), ("zerograd-zm", "f64")]
+PRODUCTION_TZ = {"f64": None, "f32": 64, "f16dev": 37}
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
+@pytest.mark.parametrize("case,store", LONG_PAIRS)
+def test_d3q27_parity_100_steps(E, case, store, kernel):
+    """FP64 to 1e-12, FP32 to 1e-5 and the FP16 deviation store to 1e-3 over 100 steps, in
+    the fused (cp.async), two-pass, re-read and tensor-copy (TMA) schedules (the last has
+    no FP64 form)."""
+    if kernel == 3 and store == "f64":
+        pytest.skip("the tensor-copy schedule runs the FP32-arithmetic stores only")
+    c = LONG_3D[case]()
+    steps = 100
+    ref = oracle_fields(("3d-long", case), c, steps)
+    tz = PRODUCTION_TZ[store] if kernel in (0, 3) else None
+    assert_parity(gpu_fields(E, c, steps, store, kernel, tz=tz), ref, TOL[store], (case, kernel, store))
 
 
 @pytest.mark.parametrize("store", ["f64", "f32", "f16dev"])

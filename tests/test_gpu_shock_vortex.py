@@ -61,3 +61,20 @@ def test_sound_wave_runs_at_the_post_shock_sound_speed(run):
         peaks[ts] = (e["r"][k], e["dp"][k])
         assert 1e-3 < e["dp"][k] < 3e-2, (ts, peaks[ts])
     assert abs((peaks[8][0] - peaks[6][0]) - expect) < 0.3, (peaks, expect)
+
+
+def test_configured_grid_with_viscosity_from_its_radius_diverges(E):
+    """The configured 1024 x 1024 case with mu from Re = 800 on r_v = 32 (mu = 0.0106)
+    leaves the physical range within 500 steps (FP64 store); with the paper's mu = 0.0198
+    the same grid stays physical over its 4000 steps (tests/test_gpu_parity.py)."""
+    c = C.shock_vortex(nx=1024, ny=1024, r_v=32.0, Ma_s=1.2, r_v_mu=32.0)
+    assert abs(c.mu0 - 0.0105830) < 1e-6
+    g = E.Solver.from_case(c, store="f64")
+    status = E.ELBM_OK
+    for _ in range(10):
+        g.step(50)
+        status = E.elbm_sync(g.h)
+        if status != E.ELBM_OK:
+            break
+    g.close()
+    assert status == E.ELBM_ERR_NONPHYSICAL
