@@ -165,6 +165,19 @@ def aggregate_rate(units_per_rank, ws, ms_max):
 
 CPU_N = 64   # side of the decaying-turbulence box the oracle is timed on
 
+# What each reduced-precision figure stands for on this workload (reported beside it).
+STORE_NOTES = {
+    "f16dev": {"meets_1e-3_tolerance": True,
+               "note": "FP16 deviations from the rest state: within the 1e-3 relative-L2 bound of the FP64 "
+                       "oracle on the parity cases over 100 steps; on this 256^3 Ma_t = 0.5 field the store "
+                       "leaves the stable range after about 34 steps (FP32 and FP64: 600+), so it is timed "
+                       "over a window of at most 20 steps after 5 warm-up steps"},
+    "bf16dev": {"meets_1e-3_tolerance": False,
+                "note": "BF16 keeps 8 significand bits: held to 8e-3 (relative L2 against the oracle), outside "
+                        "the 1e-3 bound for reduced-precision storage; leaves the stable range on this field "
+                        "after about 24 steps, timed over 10 steps after 3 warm-up steps"},
+}
+
 
 def cpu_oracle_sample(min_seconds=10.0, max_seconds=30.0, threads=None, case=None):
     """The FP64 oracle on the host cores (all of them by default) on a CPU_N^3 box of the
@@ -227,8 +240,10 @@ def run_reference(args):
     return 0
 
 
-def time_store(E, torch, case, store, steps, warmup, stream, kernel=0):
-    """Device-resident timing of `steps` steps; returns (ms_per_step, launches, solver)."""
+def time_store(E, torch, case, store, steps, warmup, stream, kernel=0, windows=1):
+    """Device-resident timing: `windows` back-to-back windows of `steps` steps each (CUDA
+    events on the launching stream, a synchronize on both sides of every window); returns
+    (ms_per_step of each window, launches per window, solver, status)."""
     g = E.Solver.from_case(case, store=store, stream=stream)
     g.set_kernel(kernel)
     for w in range(warmup):
@@ -237,20 +252,23 @@ def time_store(E, torch, case, store, steps, warmup, stream, kernel=0):
         if rc != 0:
             g.close()
             raise E.ElbmError(rc, f"warm-up step {w + 1}")
+    out = []
     l0 = g.launches
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        g.step(steps)
-        e1.record(stream)
-    e1.synchronize()
+    for _ in range(windows):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            g.step(steps)
+            e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1) / steps)
     rc = E.elbm_sync(g.h)
-    ms = e0.elapsed_time(e1) / steps
     # A state that left the stable range inside the timed window does not change the work
     # of a step (the same instructions and bytes per node); the timing stands and the
     # caller reports the status beside it.
-    return ms, g.launches - l0, g, rc
+    return out, (g.launches - l0) // windows, g, rc
 
 
 def time_e2e(E, torch, case, store, steps, stream):
@@ -274,7 +292,8 @@ def time_e2e(E, torch, case, store, steps, stream):
     tot = np.zeros(5)
     worst = 0
     t0 = time.perf_counter()
-    E._check(E.elbm_set_fields(g.h, rho, u, T), "elbm_set_fields")
+    E._check(E.elbm_set_fields(g.h, rho, u, T), "elbm_set_fields")   # synchronises
+    t1 = time.perf_counter()
     for _ in range(steps):
         g.step(1)
         # the step's totals come back every step (a non-physical status is kept, not raised:
@@ -283,14 +302,43 @@ def time_e2e(E, torch, case, store, steps, stream):
         if rc not in (0, E.ELBM_ERR_NONPHYSICAL):
             E._check(rc, "elbm_step_totals")
         worst = worst or rc
+    t2 = time.perf_counter()
     rc = E.elbm_get_fields(g.h, out[0], out[1], out[2])
     if rc not in (0, E.ELBM_ERR_NONPHYSICAL):
         E._check(rc, "elbm_get_fields")
-    el = time.perf_counter() - t0
+    t3 = time.perf_counter()
+    el = t3 - t0
     g.close()
     h2d = 5 * 8 * N / steps
     d2h = (5 * 8 * N) / steps + 5 * 8
-    return 1e3 * el / steps, h2d, d2h, worst or rc
+    breakdown = {"upload_and_init_ms": 1e3 * (t1 - t0), "steps_with_totals_ms": 1e3 * (t2 - t1),
+                 "download_ms": 1e3 * (t3 - t2), "field_bytes_each_way": 5 * 8 * N}
+    return 1e3 * el / steps, h2d, d2h, worst or rc, breakdown
+
+
+def d2q9_measure(E, torch, steps, warmup=3, side=4096):
+    """D2Q9 throughput on a periodic side^2 box (a smooth seeded field with a mean flow):
+    the default fused kernel (row march) and the one-tile-per-CTA kernel, FP32 and FP16
+    deviation stores; GLUPS and the fraction of the measured HBM peak at 144 / 72 bytes
+    per update."""
+    from paper_2102_09512_gb300 import cases as C
+    peak, _ = _peak_hbm()
+    c = C.random_smooth(2, side, side, 1, seed=4096, mu0=0.01, du=0.05, u0=(0.09, -0.07, 0.0))
+    out = {"grid": [side, side], "steps": steps}
+    for store, nbytes in (("f32", 144), ("f16dev", 72)):
+        for name, kernel in (("march", KERNELS["fused"]), ("tile", KERNELS["reread"])):
+            try:
+                ms, launches, g, rc = time_store(E, torch, c, store, steps, warmup, torch.cuda.current_stream(),
+                                                 kernel)
+                g.close()
+            except E.ElbmError as err:
+                out[f"{store}_{name}"] = {"error": str(err)}
+                continue
+            ms = ms[0]
+            glups = c.N / (ms * 1e-3) / 1e9
+            out[f"{store}_{name}"] = {"glups": glups, "ms_per_step": ms, "hbm_frac": glups * nbytes / peak,
+                                      "launches_per_step": launches / steps}
+    return out
 
 
 ENSEMBLE_MAX_STEPS = 50   # timed steps per ensemble phase (see ensemble_measure)
@@ -316,7 +364,8 @@ def ensemble_measure(E, torch, steps, store="f32"):
         ens.close()
         out["error"] = f"tuning: {err}"
         return out
-    out["schedule"] = {"tile": [32, ty], "ctas_per_sm": ctas, "grid": grid}
+    unit = {"tile": [32, ty]} if ty <= 16 else {"march_strip": 128, "rows_per_segment": ty}
+    out["schedule"] = dict(unit, ctas_per_sm=ctas, grid=grid)
     for name, mode, graph in (("persistent_graph", 0, True), ("per_instance", 1, False)):
         if ens is None:
             ens = E.Ensemble.from_cases(cases, store=store)   # the next mode starts from the initial fields
@@ -356,6 +405,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-d2q9", action="store_true")
+    ap.add_argument("--windows", type=int, default=5,
+                    help="back-to-back timed windows of --steps steps for the headline store (median reported)")
     ap.add_argument("--size", type=int, default=N_SIDE, help="box side (the bench workload is 256)")
     ap.add_argument("--kernel", default="fused", choices=sorted(KERNELS),
                     help="step schedule of the timed stores (default: the library's fused kernel)")
@@ -410,8 +462,12 @@ def main():
         sampler = ClockSampler(dev) if store == stores[0] and rank == 0 else None
         if sampler:
             sampler.start()
+        # the headline store is timed as several back-to-back windows of k steps (their
+        # median is the value, min and max are reported); the others as one window
+        windows = args.windows if store == stores[0] else 1
         try:
-            ms, launches, g, rc = time_store(E, torch, case, store, k, warm, stream, KERNELS[args.kernel])
+            ms_w, launches, g, rc = time_store(E, torch, case, store, k, warm, stream, KERNELS[args.kernel], windows)
+            ms = statistics.median(ms_w)
         except E.ElbmError as err:
             if sampler:
                 sampler.stop()
@@ -441,6 +497,11 @@ def main():
                            "hbm_frac": per_gpu_gbs / peak, "bytes_per_update": BYTES_PER_UPDATE[store],
                            "kernel_launches_per_step": launches / k,
                            "mass_total": float(totals[0]), "energy_total": float(totals[4])}
+        if windows > 1:
+            variants[store].update(windows=windows, ms_per_step_windows=ms_w, ms_per_step_min=min(ms_w),
+                                   ms_per_step_max=max(ms_w), value_is="median of the windows")
+        if store in STORE_NOTES:
+            variants[store].update(STORE_NOTES[store])
         if rc != 0:
             variants[store]["status_after_timed_steps"] = E.elbm_status_str(rc)
         if head is None and "error" not in variants[store]:
@@ -454,11 +515,15 @@ def main():
     # end-to-end through the C ABI with host buffers (headline store)
     e2e = None
     if not args.no_e2e:
-        e2e_ms, h2d, d2h, e2e_rc = time_e2e(E, torch, case, head, args.steps, stream)
+        e2e_ms, h2d, d2h, e2e_rc, breakdown = time_e2e(E, torch, case, head, args.steps, stream)
         e2e = {"value": ws * case.N / (e2e_ms * 1e-3) / 1e9, "unit": "GLUPS", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "breakdown": breakdown}
         if e2e_rc != 0:
             e2e["status"] = E.elbm_status_str(e2e_rc)
+
+    d2q9 = None
+    if not args.no_d2q9:
+        d2q9 = d2q9_measure(E, torch, args.steps)
 
     ens = None
     if not args.no_ensemble:
@@ -489,7 +554,7 @@ def main():
                    "schedule": args.kernel, "l2": "inputs larger than L2 (3.6 GB FP32 store)",
                    "parallelism": "replicas" if ws > 1 else "single-gpu"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_head,
-        "clocks": clocks, "variants": variants, "ensemble": ens,
+        "clocks": clocks, "variants": variants, "ensemble": ens, "d2q9": d2q9,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:

@@ -82,10 +82,14 @@ typedef enum { ELBM_DERIV_UPWIND = 0, ELBM_DERIV_CENTRAL = 1 } elbm_deriv;
 typedef enum {
     ELBM_KERNEL_FUSED = 0,        /* one kernel: halo-recomputed moments + collide + stream;
                                      D3Q27 FP32/FP16/BF16 prefetch each plane into shared
-                                     memory (cp.async), FP64 uses the re-read form */
+                                     memory (cp.async), FP64 uses the re-read form; D2Q9
+                                     marches strips of 128 nodes along y with the next rows
+                                     prefetched into shared memory (cp.async), or runs one
+                                     32 x 8 tile per CTA on grids too small for the march
+                                     to fill the device (see elbm_set_tile_z) */
     ELBM_KERNEL_TWOPASS = 1,      /* moment/Q~ pass into the aux buffer, then collide+stream */
     ELBM_KERNEL_FUSED_REREAD = 2, /* one kernel, D3Q27 plane gathered twice (second from L2);
-                                     D2Q9 runs the fused kernel */
+                                     D2Q9: one 32 x 8 tile per CTA, no march */
     ELBM_KERNEL_FUSED_TMA = 3     /* one kernel, D3Q27 FP32/FP16/BF16: each plane is staged in
                                      shared memory by the tensor-copy engine (TMA), one box per
                                      direction, where the boxes of a tile lie inside the grid,
@@ -174,9 +178,13 @@ int elbm_turbulence_stats(elbm_handle *h, double out[13]);
 /* Selects the kernel schedule (elbm_kernel).  Results agree to rounding. */
 int elbm_set_kernel(elbm_handle *h, int kernel);
 
-/* Length of the z segment each CTA of the fused D3Q27 kernel marches over
- * (default min(nz, 64) for FP32 stores, min(nz, 32) otherwise); a tuning knob,
- * results agree to rounding. */
+/* Length of the segment each CTA of the fused kernel marches over: z planes for
+ * D3Q27, rows (y) for D2Q9.  Chosen at elbm_create for the current device (the
+ * length that best fills the last wave of CTAs, each segment costing about two
+ * planes of prologue); a tuning knob, results agree to rounding.  D2Q9 grids with
+ * fewer 128-node strips x row segments than the device has SMs run the fused schedule
+ * as one 32 x 8 tile per CTA instead of the march; setting a segment length here
+ * selects the march for any grid. */
 int elbm_set_tile_z(elbm_handle *h, int tz);
 
 /* Raw copy of the current population store (pop_bytes) to or from host memory,
@@ -259,16 +267,20 @@ int elbm_ensemble_get_fields(elbm_ensemble *e, int k, double *rho, double *u, do
 /* Schedule: persistent (optionally replayed from a CUDA graph) or one launch per
  * instance.  Results are identical. */
 int elbm_ensemble_set_mode(elbm_ensemble *e, int mode, int use_graph);
-/* Persistent schedule: tile height (4, 8 or 16 rows of 32 nodes) and resident CTAs
- * per SM (the grid is that times the SM count, capped by the tile count). */
+/* Persistent schedule: the work unit and resident CTAs per SM (the grid is that times
+ * the SM count, capped by the unit count).  tile_y = 4, 8 or 16: one tile of 32 x tile_y
+ * nodes per unit; tile_y = 32, 64 or 128: a strip of 128 nodes of an instance marched
+ * along y over a segment of tile_y rows (next rows prefetched into shared memory). */
 int elbm_ensemble_set_schedule(elbm_ensemble *e, int tile_y, int ctas_per_sm);
 int elbm_ensemble_get_schedule(const elbm_ensemble *e, int *tile_y, int *ctas_per_sm, int *grid);
-/* Autotuner: times every (tile height, CTAs per SM) the hardware can hold over
+/* Autotuner: times every (work unit, CTAs per SM) the hardware can hold over
  * trial_steps steps each and keeps the fastest; with use_cache, a schedule tuned
  * before for the same store kind and size class (log2 of the node count) is reused.
  * The candidates write only the spare store, so the state is unchanged. */
 int elbm_ensemble_tune(elbm_ensemble *e, int trial_steps, int use_cache);
-/* Advances every instance nsteps steps (asynchronous). */
+/* Advances every instance nsteps steps (asynchronous).  With the persistent schedule and
+ * graphs on, each group of 8 steps replays one CUDA graph of 8 launches (built on first
+ * use) and the remaining steps one graph of one launch each. */
 int elbm_ensemble_step(elbm_ensemble *e, int nsteps);
 /* Synchronises and returns (and clears) the latched device status. */
 int elbm_ensemble_sync(elbm_ensemble *e);

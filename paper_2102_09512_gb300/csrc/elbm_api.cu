@@ -149,12 +149,16 @@ int elbm_create(const elbm_params* prm, elbm_handle** out) {
     h->kernel = ELBM_KERNEL_FUSED;
 
     h->kp = kp;
-    if (D == 3) {
-        // z segments sized for the waves of this device (current device at creation)
+    {
+        // z segments (D3Q27) or row segments (D2Q9) sized for the waves of this device
+        // (current device at creation)
         int dev = -1, sms = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-            h->kp.tz = choose_tz(kp, h->ops->fused_tile_y, sms, h->ops->fused_occupancy(), kp.tz);
+        {
+            if (D == 3) h->kp.tz = choose_tz(kp, h->ops->fused_tile_y, sms, h->ops->fused_occupancy(), kp.tz);
+            else plan_d2q9(h->kp, sms, h->ops->fused_occupancy());
+        }
         else
             cudaGetLastError();   // no device: keep the fallback, clear the error
     }
@@ -327,9 +331,12 @@ int elbm_set_kernel(elbm_handle* h, int kernel) {
 int elbm_set_tile_z(elbm_handle* h, int tz) {
     if (!h || tz < 1) return ELBM_ERR_ARG;
     KParams k = h->kp;
-    k.tz = tz < h->prm.nz ? tz : h->prm.nz;
+    const int planes = h->D == 3 ? h->prm.nz : h->prm.ny;   // the marched axis
+    k.tz = tz < planes ? tz : planes;
+    k.tile2d = 0;   // D2Q9: an explicit row segment selects the row march
     if (h->ops->max_blocks(k) > h->aux.max_blocks) return ELBM_ERR_ARG;   // partials would not fit
     h->kp.tz = k.tz;
+    h->kp.tile2d = 0;
     return ELBM_OK;
 }
 

@@ -1,10 +1,13 @@
 // Ensembles of independent D2Q9 instances of uneven sizes (one population store
 // holding all instances back to back), stepped either by one persistent launch over
-// the tiles of every instance (captured in a CUDA graph) or by one launch per
-// instance.  The persistent schedule (tile height and CTAs per SM) is chosen by a
-// small autotuner that times the candidates on the bound buffers.
+// the work units of every instance (replayed from CUDA graphs of several steps) or by
+// one launch per instance.  A work unit is a 32 x ty tile (ty = 4, 8, 16) or a strip of
+// kMarchW2 nodes marched along y over a segment of rows (kMarchSegs); the persistent
+// schedule (unit and CTAs per SM) is chosen by a small autotuner that times the
+// candidates on the bound buffers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <map>
@@ -23,7 +26,11 @@ namespace {
 constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 constexpr int kTileX = 32;
-constexpr int kTYs[3] = {4, 8, 16};
+constexpr int kNSched = 6;
+constexpr int kTYs[kNSched] = {4, 8, 16, kMarchSegs[0], kMarchSegs[1], kMarchSegs[2]};
+// steps per CUDA graph of the persistent schedule (even, so a replay ends in the store
+// it started from); shorter requests use one-step graphs
+constexpr int kGraphSteps = 8;
 
 const Ops* ops_2d(int store) {
     switch (store) {
@@ -35,7 +42,16 @@ const Ops* ops_2d(int store) {
     return nullptr;
 }
 
-int ty_index(int ty) { return ty == 4 ? 0 : (ty == 16 ? 2 : 1); }
+int ty_index(int ty) {
+    for (int t = 0; t < kNSched; ++t)
+        if (kTYs[t] == ty) return t;
+    return 1;
+}
+bool valid_ty(int ty) {
+    for (int t = 0; t < kNSched; ++t)
+        if (kTYs[t] == ty) return true;
+    return false;
+}
 
 // tuned schedules, cached per (store, size class = log2 of the total node count)
 std::mutex g_tune_mutex;
@@ -49,11 +65,11 @@ struct elbm_ensemble {
     const Ops* ops = nullptr;
     std::vector<KParams> kp;
     std::vector<long long> offset;             // element offsets
-    std::vector<int> tile_start[3], tiles_x[3];  // per tile height
+    std::vector<int> tile_start[kNSched], tiles_x[kNSched];  // work units per schedule
     long long total_nodes = 0, max_nodes = 0;
     size_t pop_bytes = 0;
     // aux layout
-    size_t a_status = 0, a_params = 0, a_offset = 0, a_tstart[3] = {0, 0, 0}, a_tx[3] = {0, 0, 0};
+    size_t a_status = 0, a_params = 0, a_offset = 0, a_tstart[kNSched] = {}, a_tx[kNSched] = {};
     size_t a_qfield = 0, a_partials = 0, a_staging = 0, aux_bytes = 0;
     int max_blocks = 0;
     // binding
@@ -64,9 +80,10 @@ struct elbm_ensemble {
     int cur = 0;
     // schedule
     int mode = ELBM_ENSEMBLE_PERSISTENT;
-    int ty = 8, ctas_per_sm = 2, grid = 0;
+    int ty = kMarchSegs[1], ctas_per_sm = 2, grid = 0;
     bool use_graph = true;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step from store c to store 1-c
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};    // one step from store c to store 1-c
+    cudaGraphExec_t graphk[2] = {nullptr, nullptr};   // kGraphSteps steps from store c back to c
     long long steps = 0, launches = 0;
 
     int* status() { return (int*)(aux + a_status); }
@@ -83,11 +100,12 @@ struct elbm_ensemble {
         return a;
     }
     void drop_graphs() {
-        for (auto& g : graph)
-            if (g) {
-                cudaGraphExecDestroy(g);
-                g = nullptr;
-            }
+        for (auto* gs : {graph, graphk})
+            for (int c = 0; c < 2; ++c)
+                if (gs[c]) {
+                    cudaGraphExecDestroy(gs[c]);
+                    gs[c] = nullptr;
+                }
     }
 };
 
@@ -126,8 +144,8 @@ cudaError_t launch_persistent(elbm_ensemble* e, const void* src, void* dst, cuda
     return e->ops->step_ensemble(e->args(ty_index(e->ty)), src, dst, e->status(), e->ty, e->grid, s, &e->launches);
 }
 
-// graph of one persistent step from store c to store 1-c
-cudaError_t build_graph(elbm_ensemble* e, int c) {
+// graph of `steps` persistent steps starting from store c (alternating stores)
+cudaError_t build_graph(elbm_ensemble* e, int c, int steps, cudaGraphExec_t* out) {
     cudaStream_t cap;
     cudaError_t err = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     if (err != cudaSuccess) return err;
@@ -135,12 +153,14 @@ cudaError_t build_graph(elbm_ensemble* e, int c) {
     err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (err == cudaSuccess) {
         const long long before = e->launches;
-        cudaError_t le = launch_persistent(e, e->pop[c], e->pop[1 - c], cap);
+        cudaError_t le = cudaSuccess;
+        for (int s = 0; s < steps && le == cudaSuccess; ++s)
+            le = launch_persistent(e, e->pop[(c + s) & 1], e->pop[(c + s + 1) & 1], cap);
         e->launches = before;   // counted when the graph is launched
         err = cudaStreamEndCapture(cap, &g);
         if (err == cudaSuccess) err = le;
     }
-    if (err == cudaSuccess) err = cudaGraphInstantiate(&e->graph[c], g, 0);
+    if (err == cudaSuccess) err = cudaGraphInstantiate(out, g, 0);
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cap);
     return err;
@@ -157,7 +177,7 @@ int step_once(elbm_ensemble* e) {
                                      (double*)(e->aux + e->a_partials), &nb, e->status(), e->stream, &e->launches);
         }
     } else if (e->use_graph) {
-        if (!e->graph[c]) err = build_graph(e, c);
+        if (!e->graph[c]) err = build_graph(e, c, 1, &e->graph[c]);
         if (err == cudaSuccess) err = cudaGraphLaunch(e->graph[c], e->stream);
         ++e->launches;
     } else {
@@ -197,12 +217,13 @@ int elbm_ensemble_create(const elbm_params* params, int n, elbm_ensemble** out) 
         if (e->kp[k].N > e->max_nodes) e->max_nodes = e->kp[k].N;
     }
     if (e->total_nodes > (1LL << 31)) { delete e; return ELBM_ERR_UNSUPPORTED; }
-    for (int t = 0; t < 3; ++t) {
+    for (int t = 0; t < kNSched; ++t) {
         e->tile_start[t].resize(n + 1);
         e->tiles_x[t].resize(n);
+        const int width = kTYs[t] > 16 ? kMarchW2 : kTileX;   // march strips or tiles
         int acc = 0;
         for (int k = 0; k < n; ++k) {
-            const int txn = (e->kp[k].nx + kTileX - 1) / kTileX, tyn = (e->kp[k].ny + kTYs[t] - 1) / kTYs[t];
+            const int txn = (e->kp[k].nx + width - 1) / width, tyn = (e->kp[k].ny + kTYs[t] - 1) / kTYs[t];
             e->tile_start[t][k] = acc;
             e->tiles_x[t][k] = txn;
             acc += txn * tyn;
@@ -211,9 +232,13 @@ int elbm_ensemble_create(const elbm_params* params, int n, elbm_ensemble** out) 
     }
     e->pop_bytes = (size_t)off * ops->value_bytes * 2;
     // aux layout
+    // per-CTA partials of the one-launch-per-instance mode: its row segments are chosen
+    // for the device at bind, no shorter than 16 rows, so size for that
     int maxb = 0;
     for (int k = 0; k < n; ++k) {
-        const int b = ops->max_blocks(e->kp[k]);
+        KParams shortest = e->kp[k];
+        shortest.tz = shortest.ny < 16 ? shortest.ny : 16;
+        const int b = std::max(ops->max_blocks(e->kp[k]), ops->max_blocks(shortest));
         if (b > maxb) maxb = b;
     }
     e->max_blocks = maxb;
@@ -221,7 +246,7 @@ int elbm_ensemble_create(const elbm_params* params, int n, elbm_ensemble** out) 
     e->a_status = o; o = align_up(o + sizeof(int));
     e->a_params = o; o = align_up(o + (size_t)n * sizeof(KParams));
     e->a_offset = o; o = align_up(o + (size_t)n * sizeof(long long));
-    for (int t = 0; t < 3; ++t) {
+    for (int t = 0; t < kNSched; ++t) {
         e->a_tstart[t] = o; o = align_up(o + (size_t)(n + 1) * sizeof(int));
         e->a_tx[t] = o; o = align_up(o + (size_t)n * sizeof(int));
     }
@@ -229,7 +254,7 @@ int elbm_ensemble_create(const elbm_params* params, int n, elbm_ensemble** out) 
     e->a_qfield = o; o = align_up(o + (size_t)2 * e->max_nodes * ops->real_bytes);
     e->a_staging = o; o = align_up(o + (size_t)4 * e->max_nodes * sizeof(double));
     e->aux_bytes = o;
-    set_schedule(e, 8, 2);
+    set_schedule(e, kMarchSegs[1], 2);
     e->grid = 0;   // set at bind (needs the device)
     *out = e;
     return ELBM_OK;
@@ -252,6 +277,9 @@ int elbm_ensemble_bind(elbm_ensemble* e, void* pop_a, void* pop_b, void* aux, vo
     e->stream = (cudaStream_t)stream;
     e->cur = 0;
     e->bound = true;
+    // the one-launch-per-instance mode runs each instance as a single lattice would on this device
+    const int sms = sm_count(), occ = e->ops->fused_occupancy();
+    for (KParams& k : e->kp) plan_d2q9(k, sms, occ);
     cudaError_t c = cudaMemsetAsync(e->status(), 0, sizeof(int), e->stream);
     if (c == cudaSuccess)
         c = cudaMemcpyAsync(e->aux + e->a_params, e->kp.data(), e->kp.size() * sizeof(KParams),
@@ -259,7 +287,7 @@ int elbm_ensemble_bind(elbm_ensemble* e, void* pop_a, void* pop_b, void* aux, vo
     if (c == cudaSuccess)
         c = cudaMemcpyAsync(e->aux + e->a_offset, e->offset.data(), e->offset.size() * sizeof(long long),
                             cudaMemcpyHostToDevice, e->stream);
-    for (int t = 0; t < 3 && c == cudaSuccess; ++t) {
+    for (int t = 0; t < kNSched && c == cudaSuccess; ++t) {
         c = cudaMemcpyAsync(e->aux + e->a_tstart[t], e->tile_start[t].data(), (e->n + 1) * sizeof(int),
                             cudaMemcpyHostToDevice, e->stream);
         if (c == cudaSuccess)
@@ -312,7 +340,7 @@ int elbm_ensemble_set_mode(elbm_ensemble* e, int mode, int use_graph) {
 }
 
 int elbm_ensemble_set_schedule(elbm_ensemble* e, int tile_y, int ctas_per_sm) {
-    if (!e || (tile_y != 4 && tile_y != 8 && tile_y != 16) || ctas_per_sm < 1 || ctas_per_sm > 32) return ELBM_ERR_ARG;
+    if (!e || !valid_ty(tile_y) || ctas_per_sm < 1 || ctas_per_sm > 32) return ELBM_ERR_ARG;
     set_schedule(e, tile_y, ctas_per_sm);
     return ELBM_OK;
 }
@@ -347,7 +375,7 @@ int elbm_ensemble_tune(elbm_ensemble* e, int trial_steps, int use_cache) {
     int best_ty = 8, best_c = 1;
     const long long launches0 = e->launches;
     int rc = ELBM_OK;
-    for (int t = 0; t < 3 && rc == ELBM_OK; ++t) {
+    for (int t = 0; t < kNSched && rc == ELBM_OK; ++t) {
         const int ty = kTYs[t];
         const int occ = e->ops->ensemble_occupancy(ty);
         for (int c = 1; c <= occ && rc == ELBM_OK; ++c) {
@@ -377,7 +405,21 @@ int elbm_ensemble_tune(elbm_ensemble* e, int trial_steps, int use_cache) {
 
 int elbm_ensemble_step(elbm_ensemble* e, int nsteps) {
     if (!e || !e->bound || nsteps < 0) return ELBM_ERR_ARG;
-    for (int s = 0; s < nsteps; ++s) {
+    int s = 0;
+    if (e->mode == ELBM_ENSEMBLE_PERSISTENT && e->use_graph) {
+        // whole groups of kGraphSteps steps from one graph each (the store parity is back
+        // where it started after each group)
+        for (; s + kGraphSteps <= nsteps; s += kGraphSteps) {
+            const int c = e->cur;
+            cudaError_t err = cudaSuccess;
+            if (!e->graphk[c]) err = build_graph(e, c, kGraphSteps, &e->graphk[c]);
+            if (err == cudaSuccess) err = cudaGraphLaunch(e->graphk[c], e->stream);
+            if (err != cudaSuccess) return ELBM_ERR_CUDA;
+            e->launches += kGraphSteps;
+            e->steps += kGraphSteps;
+        }
+    }
+    for (; s < nsteps; ++s) {
         const int rc = step_once(e);
         if (rc != ELBM_OK) return rc;
     }

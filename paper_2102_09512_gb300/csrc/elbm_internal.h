@@ -127,9 +127,14 @@ inline int fill_kparams(const elbm_params& p, KParams& k, int* D_out) {
         }
     }
     // z segment of the fused D3Q27 kernels: longer for FP32 (one CTA per SM, so
-    // fewer prologues per plane matter more), measured at 256^3
-    const int tz = p.store == ELBM_F32 ? 64 : 32;
-    k.tz = p.nz < tz ? p.nz : tz;
+    // fewer prologues per plane matter more), measured at 256^3; D2Q9: rows per
+    // segment of the row march (both refined for the device at handle creation)
+    if (D == 3) {
+        const int tz = p.store == ELBM_F32 ? 64 : 32;
+        k.tz = p.nz < tz ? p.nz : tz;
+    } else {
+        k.tz = p.ny < 32 ? p.ny : 32;
+    }
     if (dev) {
         // Rest state f^eq(rho_ref, 0, T_ref), g^eq(rho_ref, 0, T_ref): with u = 0 the
         // per-axis factors are phi = (T/2, 1-T, T/2) and psi = (T^2/2, -T^2, T^2/2).
@@ -195,6 +200,12 @@ inline NoallocLayout noalloc_layout(long long N, int D, size_t real_bytes) {
     return l;
 }
 
+// D2Q9 row march: a CTA owns a strip of kMarchW2 nodes of a row and marches along y;
+// the persistent ensemble runs it with segments of one of kMarchSegs rows (a schedule
+// value above 16; 4, 8 and 16 select the one-tile-per-unit kernel with 32 x ty tiles).
+constexpr int kMarchW2 = 128;
+constexpr int kMarchSegs[3] = {32, 64, 128};
+
 // Layout of the auxiliary buffer (all offsets 256-byte aligned).
 struct AuxLayout {
     size_t status;      // int32 status word
@@ -252,7 +263,7 @@ struct Ops {
     int (*ensemble_occupancy)(int ty);
     cudaError_t (*stats)(const KParams& p, const void* pop, double* partials, int* nblocks, cudaStream_t s,
                          long long* launches);   // kStatsSums partial sums per CTA
-    int fused_tile_y;             // tile height of the fused kernels (tile width 32)
+    int fused_tile_y;             // D3Q27: tile height of the fused kernels (tile width 32); D2Q9: 1 (row march)
     int (*fused_occupancy)();     // resident CTAs per SM of the default fused D3Q27 kernel (0: unknown)
     cudaError_t (*step_fused_tma)(const KParams& p, const void* src, void* dst, const CUtensorMap* src_map,
                                   double* partials, int* nblocks, int* status, cudaStream_t s, long long* launches);
@@ -266,18 +277,17 @@ struct Ops {
 // of the last wave times tz / (tz + 2), the second factor charging each segment about
 // two planes of prologue (the Q~ plane below it and the plane above it).  Ties keep
 // the longer segment.  Without device information the fallback is kept.
-inline int choose_tz(const KParams& k, int ty, int sms, int per_sm, int fallback) {
-    if (sms <= 0 || per_sm <= 0) return fallback < k.nz ? fallback : k.nz;
-    const double tiles = (double)((k.nx + 31) / 32) * (double)((k.ny + ty - 1) / ty);
+inline int choose_segment(double tiles, int nplanes, int sms, int per_sm, int fallback) {
+    if (sms <= 0 || per_sm <= 0) return fallback < nplanes ? fallback : nplanes;
     const double slots = (double)sms * per_sm;
-    const int lo = k.nz < 16 ? k.nz : 16, hi = 128;
-    int best = fallback < k.nz ? fallback : k.nz;
+    const int lo = nplanes < 16 ? nplanes : 16, hi = 128;
+    int best = fallback < nplanes ? fallback : nplanes;
     double best_score = -1.0;
-    for (int nseg = 1; nseg <= k.nz; ++nseg) {
-        const int tz = (k.nz + nseg - 1) / nseg;
+    for (int nseg = 1; nseg <= nplanes; ++nseg) {
+        const int tz = (nplanes + nseg - 1) / nseg;
         if (tz > hi) continue;
         if (tz < lo) break;
-        const int ns = (k.nz + tz - 1) / tz;
+        const int ns = (nplanes + tz - 1) / tz;
         const double waves = tiles * ns / slots;
         const double fill = waves / std::ceil(waves);
         const double score = fill * tz / (tz + 2.0);
@@ -287,6 +297,23 @@ inline int choose_tz(const KParams& k, int ty, int sms, int per_sm, int fallback
         }
     }
     return best;
+}
+inline int choose_tz(const KParams& k, int ty, int sms, int per_sm, int fallback) {
+    const double tiles = (double)((k.nx + 31) / 32) * (double)((k.ny + ty - 1) / ty);
+    return choose_segment(tiles, k.nz, sms, per_sm, fallback);
+}
+// The same choice for the D2Q9 row march: strips of kMarchW2 nodes, segments of rows.
+inline int choose_rows(const KParams& k, int sms, int per_sm, int fallback) {
+    return choose_segment((double)((k.nx + kMarchW2 - 1) / kMarchW2), k.ny, sms, per_sm, fallback);
+}
+// D2Q9 schedule for a device of `sms` SMs: the row segment, and whether the grid is too
+// small for the march (fewer strips x segments than SMs), in which case the default fused
+// schedule runs the one-tile-per-CTA kernel instead.  Without device information the
+// march with the fallback segment is kept.
+inline void plan_d2q9(KParams& k, int sms, int per_sm) {
+    k.tz = choose_rows(k, sms, per_sm, k.tz);
+    const long long ctas = (long long)((k.nx + kMarchW2 - 1) / kMarchW2) * ((k.ny + k.tz - 1) / k.tz);
+    k.tile2d = sms > 0 && ctas < sms;
 }
 
 const Ops* ops_d2_f64();

@@ -82,6 +82,23 @@ __device__ __forceinline__ R fixed_Q(const KParams& p, int a) {
     else return p.fixQf[a];
 }
 
+// Directions of node (x, y) whose pull source lies beyond a fixed-state face (D2Q9;
+// bit i for direction i): their pairs are the fixed state's, not a stored node's.
+__device__ __forceinline__ unsigned fixed_mask(const KParams& p, int x, int y) {
+    unsigned m = 0u;
+    if constexpr (kD == 2) {
+        if (p.has_fixed) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    if (beyond_fixed(p, 0, x + 1 - a, p.nx) || beyond_fixed(p, 1, y + 1 - b, p.ny))
+                        m |= 1u << (a + 3 * b);
+        }
+    }
+    return m;
+}
+
 // With PULL = false every direction is read at the node itself (no streaming);
 // that form is used once, to collide the initial state.
 template <bool PULL = true>
@@ -100,17 +117,7 @@ __device__ __forceinline__ void pull_rows(const KParams& p, int x, int y, int z,
 #pragma unroll
         for (int b = 0; b < 3; ++b)
             r.row[b][c] = p.nx * (ys[b] + p.ny * zs[c]);
-    r.gmask = 0;
-    if constexpr (kD == 2 && PULL) {
-        if (p.has_fixed) {
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    if (beyond_fixed(p, 0, x + 1 - a, p.nx) || beyond_fixed(p, 1, y + 1 - b, p.ny))
-                        r.gmask |= 1u << (a + 3 * b);
-        }
-    }
+    r.gmask = PULL ? fixed_mask(p, x, y) : 0u;
 }
 
 // Address of the pair of direction i pulled by node r in store s.
@@ -252,6 +259,11 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// Waits until at most N of this thread's most recent cp.async groups are still pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait_pending() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // ---------------------------------------------------------------------------
 // initial state and field extraction
@@ -1231,14 +1243,278 @@ fused3d_reread_kernel(const __grid_constant__ KParams p, const P* __restrict__ s
 }
 
 // ---------------------------------------------------------------------------
+// D2Q9, row march
+// ---------------------------------------------------------------------------
+// The two-dimensional form of the pipelined D3Q27 kernel: a CTA of W threads owns a
+// strip of W nodes of a row and marches along y over a segment of rows [y0, ye); the
+// row plays the part of the plane.  For every row it needs the pulled pairs of its W
+// nodes and of the two nodes at the strip's ends (the halo of the x derivative);
+// they are copied with cp.async into one of two shared-memory row buffers one row ahead
+// ([direction][slot], slot 0 the left end, 1..W the strip, W+1 or the ragged end + 1
+// the right end).  Each thread copies and reads only its own slots; the Q~_xxx row
+// (double-buffered by row parity) is the only shared array, so one barrier per row
+// orders it.  Q~_yyy of the rows below, at and above the current one rolls in registers.
+// Per row y: wait for this thread's copies of row y+1; barrier; read row y's pairs into
+// registers and request row y+2 into their slots; moments of row y+1 (strip and ends)
+// -> Q~ (registers kept for the next row); collide row y and store.  Every population
+// leaves HBM once per step; a segment re-reads about two rows (the row below it and
+// the row above it).
+template <int W, int NB = 2>
+struct March2 {
+    static constexpr int NS = W + 2;
+    static constexpr int NBUF = NB;   // row buffers: rows y (collide), y+1 (moments), up to y+NB-1 in flight
+    static constexpr size_t buf_bytes = (size_t)NB * Q * NS * sizeof(P);
+    static constexpr size_t q_bytes = (size_t)2 * NS * sizeof(R);
+    static constexpr size_t smem_bytes = buf_bytes + q_bytes;
+};
+
+// Per-direction plane bases of one lattice's stores: from the kernel parameters (one
+// lattice), or formed from the instance's base (ensemble).
+struct PlanesParam {
+    const DirPlanes* pl;
+    const P* base;
+    __device__ __forceinline__ const P* s(int i) const { return pl->src[i]; }
+    __device__ __forceinline__ P* d(int i) const { return pl->dst[i]; }
+};
+struct PlanesBase {
+    const P* src;
+    P* dst;
+    size_t N;
+    const P* base;
+    __device__ __forceinline__ const P* s(int i) const { return src + (size_t)i * N; }
+    __device__ __forceinline__ P* d(int i) const { return dst + (size_t)i * N; }
+};
+
+// Q~_yyy of node (x, y) (y mapped) by a direct gather, with the fixed-state pairs where
+// its pulls cross a fixed face (used once per segment).
+template <bool CAL>
+__device__ __forceinline__ R direct_anomaly_y(const KParams& p, const P* __restrict__ src, int x, int y) {
+    PullRows r;
+    pull_rows(p, x, y, 0, r);
+    R f[Q], g[Q];
+    gather(p, src, r, f, g);
+    Moments<R> m;
+    node_moments<kD, R, false, DEV, CAL>(f, g, p, m);
+    return anomaly(m.rho, m.uy, m.T);
+}
+
+template <int W, int NB, bool CAL, class PL>
+__device__ __forceinline__ void march2d_segment(const KParams& p, const PL& pl, int x0, int y0, int ye,
+                                                unsigned char* smem, Acc5& acc, bool& bad) {
+    using MC = March2<W, NB>;
+    static_assert(NB == 2 || NB == 3, "two or three row buffers");
+    constexpr int NS = MC::NS;
+    P* buf = reinterpret_cast<P*>(smem);                   // [NB][Q][NS]
+    R* qxs = reinterpret_cast<R*>(smem + MC::buf_bytes);   // [2][NS]
+    const int t = threadIdx.x;
+    const int x = x0 + t;
+    const bool active = x < p.nx;
+    const int xl = min(x0 + W, p.nx) - 1 - x0;   // last local column of the strip
+    const int nslot = t + 1;
+    // the strip's ends: thread 0 the left one (slot 0), thread 1 the right one (slot xl + 2);
+    // beyond a fixed-state face an end carries the fixed state's Q~ and is not copied
+    const bool has_halo = t < 2;
+    const int hux = t == 0 ? x0 - 1 : x0 + xl + 1;
+    const int hx = map_axis(hux, p.nx, p.per_x);
+    const bool hfixed = has_halo && p.has_fixed && beyond_fixed(p, 0, hux, p.nx);
+    const int hslot = t == 0 ? 0 : xl + 2;
+
+    auto issue_row = [&](int yq, int sb, bool with_halo) {   // yq already mapped
+        P* bb = buf + (size_t)sb * Q * NS;
+        if (active) {
+            PullRows r;
+            pull_rows(p, x, yq, 0, r);
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                cp_async<sizeof(P)>(bb + i * NS + nslot, pl.s(i) + (unsigned)(r.row[(i / 3) % 3][1] + r.xs[i % 3]));
+        }
+        if (with_halo && has_halo && !hfixed) {
+            PullRows r;
+            pull_rows(p, hx, yq, 0, r);
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                cp_async<sizeof(P)>(bb + i * NS + hslot, pl.s(i) + (unsigned)(r.row[(i / 3) % 3][1] + r.xs[i % 3]));
+        }
+        cp_async_commit();
+    };
+    // moments of the node in slot `slot` of buffer sb; gm marks the pairs that are the
+    // fixed state's (pulled across a fixed face)
+    auto row_moments = [&](int sb, int slot, unsigned gm, Moments<R>& m, auto full) {
+        const P* bb = buf + (size_t)sb * Q * NS + slot;
+        if constexpr (DEV) {
+            if (!gm) {   // sums straight from the stored pairs
+                node_moments_stored<kD, kST, decltype(full)::value, CAL>([&](int i) { return bb[i * NS]; }, p, m);
+                return;
+            }
+        }
+        R f[Q], g[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Cd::dec(bb[i * NS], f[i], g[i]);
+        if (gm) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                if ((gm >> i) & 1u) fixed_pair(p, i, f[i], g[i]);
+        }
+        node_moments<kD, R, decltype(full)::value, DEV, CAL>(f, g, p, m);
+    };
+    using Full = std::true_type;
+    using Lite = std::false_type;
+    auto QX = [&](int b, int slot) -> R& { return qxs[b * NS + slot]; };
+    auto halo_q = [&](int sb, int yq) {
+        if (hfixed) return fixed_Q(p, 0);
+        Moments<R> hm;
+        row_moments(sb, hslot, fixed_mask(p, hx, yq), hm, Lite());
+        return anomaly(hm.rho, hm.ux, hm.T);
+    };
+
+    // prologue: Q~_yyy of the row below the segment, rows y0 and y0+1 in flight, moments of y0
+    R qy_prev = R(0), qy_cur = R(0), qy_next = R(0);
+    if (active) {
+        if (p.has_fixed && beyond_fixed(p, 1, y0 - 1, p.ny)) qy_prev = fixed_Q(p, 1);
+        else qy_prev = direct_anomaly_y<CAL>(p, pl.base, x, map_axis(y0 - 1, p.ny, p.per_y));
+    }
+    // rows y0 .. y0+NB-1 in flight (a row past ye is not needed; its group stays empty)
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (y0 + j <= ye) issue_row(map_axis(y0 + j, p.ny, p.per_y), j, y0 + j < ye);
+        else cp_async_commit();
+    }
+    Moments<R> m_cur, m_next;
+    cp_async_wait_pending<NB - 1>();   // row y0 has landed
+    __syncthreads();
+    if (active) {
+        row_moments(0, nslot, fixed_mask(p, x, y0), m_cur, Full());
+        QX(0, nslot) = anomaly(m_cur.rho, m_cur.ux, m_cur.T);
+        qy_cur = anomaly(m_cur.rho, m_cur.uy, m_cur.T);
+    }
+    if (has_halo) QX(0, hslot) = halo_q(0, y0);
+
+    for (int y = y0; y < ye; ++y) {
+        const int k = y - y0;
+        const int bq = k & 1;                          // Q~ row of y (y+1: bq ^ 1)
+        const int sz = k % NB, sn = (k + 1) % NB;      // row buffers of rows y and y+1
+        const bool last = (y + 1 == ye);
+        cp_async_wait_pending<NB - 2>();               // row y+1 has landed (y+2.. may be in flight)
+        __syncthreads();
+        P pk[Q];   // the pulled pairs of row y, as stored
+        if (active) {
+            const P* bb = buf + (size_t)sz * Q * NS + nslot;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) pk[i] = bb[i * NS];
+        }
+        if (y + NB <= ye) issue_row(map_axis(y + NB, p.ny, p.per_y), sz, y + NB < ye);
+        else cp_async_commit();   // keep one group per row for the wait count
+
+        const int yn = map_axis(y + 1, p.ny, p.per_y);
+        if (active) {
+            if (p.has_fixed && beyond_fixed(p, 1, y + 1, p.ny)) {
+                qy_next = fixed_Q(p, 1);   // the last row of the grid: nothing after it
+            } else {
+                row_moments(sn, nslot, fixed_mask(p, x, yn), m_next, Full());
+                qy_next = anomaly(m_next.rho, m_next.uy, m_next.T);
+                if (!last) QX(bq ^ 1, nslot) = anomaly(m_next.rho, m_next.ux, m_next.T);
+            }
+        }
+        if (!last && has_halo) QX(bq ^ 1, hslot) = halo_q(sn, yn);
+
+        if (active) {
+            bad |= nonphysical(m_cur);
+            const R Dx = dQ(p.deriv, m_cur.ux, QX(bq, nslot - 1), QX(bq, nslot), QX(bq, nslot + 1));
+            const R Dy = dQ(p.deriv, m_cur.uy, qy_prev, qy_cur, qy_next);
+            R v[5];
+            node_totals(m_cur, m_cur.rE, v);
+            acc.add(v);
+            Relax<kD, R, DEV, CAL> rx;
+            rx.init(m_cur, Dx, Dy, R(0), p);
+            const unsigned gm = fixed_mask(p, x, y);
+            const unsigned n = (unsigned)(x + p.nx * y);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                R f, g;
+                Cd::dec(pk[i], f, g);
+                if ((gm >> i) & 1u) fixed_pair(p, i, f, g);
+                pl.d(i)[n] = Cd::enc(rx.f(i, f, p), rx.g(i, g, p));
+            }
+        }
+        m_cur = m_next;
+        qy_prev = qy_cur;
+        qy_cur = qy_next;
+    }
+    cp_async_wait_all();
+    __syncthreads();   // the shared buffers are reused by the next segment of a persistent CTA
+}
+
+// One lattice: CTA (bx, by) marches strip bx over rows [by * p.tz, min((by + 1) * p.tz, ny)).
+template <int W, int NB, bool CAL>
+__global__ void __launch_bounds__(W)
+march2d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPlanes pl, const P* __restrict__ src,
+               double* __restrict__ partials, int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char march_smem[];
+    const int x0 = blockIdx.x * W, y0 = blockIdx.y * p.tz, ye = min(y0 + p.tz, p.ny);
+    Acc5 acc;
+    acc.zero();
+    bool bad = false;
+    march2d_segment<W, NB, CAL>(p, PlanesParam{&pl, src}, x0, y0, ye, march_smem, acc, bad);
+    flag_if(bad, status);
+    R tot[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) tot[k] = acc.s[k] - acc.c[k];
+    block_sum5_warp(tot, partials + 5 * (blockIdx.x + gridDim.x * blockIdx.y));
+}
+
+// Persistent ensemble step on the row march: the work list holds (instance, strip, segment)
+// units (instance k owns units [tile_start[k], tile_start[k+1]), tiles_x[k] strips per
+// segment row); CTA b takes units b, b + gridDim.x, ...  No totals are kept.
+template <int W, int NB, bool CAL>
+__global__ void __launch_bounds__(W)
+ensemble_march2d_kernel(const EnsembleArgs a, const P* __restrict__ src, P* __restrict__ dst, int seg,
+                        int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char march_smem[];
+    __shared__ int s_start[kMaxEnsemble + 1];
+    __shared__ int s_tx[kMaxEnsemble];
+    for (int k = threadIdx.x; k <= a.n; k += W) s_start[k] = a.tile_start[k];
+    for (int k = threadIdx.x; k < a.n; k += W) s_tx[k] = a.tiles_x[k];
+    __syncthreads();
+    bool bad = false;
+    Acc5 acc;
+    acc.zero();
+    int k = 0;
+    for (int u = blockIdx.x; u < a.ntiles; u += gridDim.x) {
+        while (u >= s_start[k + 1]) ++k;   // u increases, so k only moves forward
+        const int local = u - s_start[k];
+        const int bx = local % s_tx[k], by = local / s_tx[k];
+        const KParams& p = a.params[k];
+        const long long off = a.offset[k];
+        const int y0 = by * seg;
+        march2d_segment<W, NB, CAL>(p, PlanesBase{src + off, dst + off, (size_t)p.N, src + off}, bx * W, y0,
+                                min(y0 + seg, p.ny), march_smem, acc, bad);
+    }
+    flag_if(bad, status);
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 constexpr int kThreads = kThreads1D;
-constexpr int kTY2 = 8;                  // D2Q9 fused tile 32 x 8
+constexpr int kTY2 = 8;                  // D2Q9 tile kernel: 32 x 8 tiles
+constexpr int kW2 = kMarchW2;            // D2Q9 row march: strips of kW2 nodes
+#ifndef ELBM_MARCH_NB
+#define ELBM_MARCH_NB 2
+#endif
+constexpr int kNBM = ELBM_MARCH_NB;      // row buffers of the march (2: one row in flight, 3: two)
+using MarchCfg = March2<kW2, kNBM>;
 #ifndef ELBM_TY3
 #define ELBM_TY3 8
 #endif
-constexpr int kTY3 = ELBM_TY3;           // D3Q27 fused tiles 32 x kTY3
+constexpr int kTY3 = ELBM_TY3;           // D3Q27 re-read and tensor-copy kernels: tiles 32 x kTY3
+// Pipelined (cp.async) D3Q27 kernel: tiles 32 x kTYP.  Taller FP32 tiles (more warps per
+// SM, relatively fewer halo nodes) measured slower at 256^3: 10 rows 7 %, 12 rows 37 %
+// (their plane buffers leave the L1 cache that the 8-byte cp.async copies go through
+// 60 KB and 28 KB instead of about 90 KB, and cap the registers at 168); 8 it is.
+#ifndef ELBM_TYP_F32
+#define ELBM_TYP_F32 8
+#endif
+constexpr int kTYP = (kST == ST_F32) ? ELBM_TYP_F32 : kTY3;
 constexpr int kTotalsBlocks = 2 * 152;   // totals_kernel grid (grid-stride)
 // Pipelined D3Q27 kernel per store: two plane buffers.  FP32 pairs make them 145 KB
 // (one CTA per SM, up to 255 registers; a third buffer would leave L1 almost no
@@ -1255,8 +1531,8 @@ constexpr int kTotalsBlocks = 2 * 152;   // totals_kernel grid (grid-stride)
 #endif
 constexpr bool kPipe = (kST != ST_F64);
 constexpr int kNB = (kST == ST_F32) ? ELBM_PIPE_NB_F32 : ELBM_PIPE_NB_F16;
-constexpr int kMinB = (PipeBytes<kTY3, kNB>::value * 2 + 2048 <= 228 * 1024) ? 2 : 1;
-using PipeCfg = Pipe<kTY3, kNB>;
+constexpr int kMinB = (PipeBytes<kTYP, kNB>::value * 2 + 2048 <= 228 * 1024) ? 2 : 1;
+using PipeCfg = Pipe<kTYP, kNB>;
 #ifndef ELBM_EARLY
 #define ELBM_EARLY 1
 #endif
@@ -1305,16 +1581,28 @@ int encode_tmap(const KParams& p, const void* base, CUtensorMap* out) {
 
 inline unsigned blocks_1d(long long n) { return (unsigned)blocks_1d_of(n); }
 
+// Grid of the default fused kernel: D2Q9 row march (strips x row segments of p.tz rows),
+// D3Q27 pipelined kernel (32 x kTYP column tiles x z segments of p.tz planes).
 dim3 fused_grid(const KParams& p) {
-    if (kD == 2) return dim3((p.nx + TX - 1) / TX, (p.ny + kTY2 - 1) / kTY2, 1);
+    if (kD == 2) return dim3((p.nx + kW2 - 1) / kW2, (p.ny + p.tz - 1) / p.tz, 1);
+    const int ty = kPipe ? kTYP : kTY3;
+    return dim3((p.nx + TX - 1) / TX, (p.ny + ty - 1) / ty, (p.nz + p.tz - 1) / p.tz);
+}
+// Grid of the D3Q27 re-read and tensor-copy kernels (32 x kTY3 tiles).
+dim3 grid3_ty3(const KParams& p) {
     return dim3((p.nx + TX - 1) / TX, (p.ny + kTY3 - 1) / kTY3, (p.nz + p.tz - 1) / p.tz);
 }
+// Grid of the D2Q9 tile kernel (the re-read schedule of D2Q9): 32 x kTY2 tiles.
+dim3 tile2d_grid(const KParams& p) { return dim3((p.nx + TX - 1) / TX, (p.ny + kTY2 - 1) / kTY2, 1); }
 
 int max_blocks(const KParams& p) {
     long long a = blocks_1d(p.N);
     dim3 gf = fused_grid(p);
     long long b = (long long)gf.x * gf.y * gf.z;
     long long m = a > b ? a : b;
+    const dim3 gt = kD == 2 ? tile2d_grid(p) : grid3_ty3(p);
+    const long long c = (long long)gt.x * gt.y * gt.z;
+    if (c > m) m = c;
     if (m < kTotalsBlocks) m = kTotalsBlocks;
     return (int)m;
 }
@@ -1360,12 +1648,26 @@ cudaError_t launch_fused_cal(const KParams& p, const void* src, void* dst, doubl
                              cudaStream_t s, bool reread) {
     const dim3 grid = fused_grid(p);
     if constexpr (DD == 2) {
-        fused2d_kernel<kTY2, CAL><<<grid, dim3(TX, kTY2), 0, s>>>(p, (const P*)src, (P*)dst, partials, status);
+        if (reread || p.tile2d) {   // the tile kernel: one 32 x kTY2 tile per CTA, no march
+            fused2d_kernel<kTY2, CAL><<<tile2d_grid(p), dim3(TX, kTY2), 0, s>>>(p, (const P*)src, (P*)dst, partials,
+                                                                               status);
+        } else {
+            auto kern = march2d_kernel<kW2, kNBM, CAL>;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)MarchCfg::smem_bytes);
+            if (e != cudaSuccess) return e;
+            DirPlanes pl;
+            for (int i = 0; i < Q; ++i) {
+                pl.src[i] = (const P*)src + (size_t)i * (size_t)p.N;
+                pl.dst[i] = (P*)dst + (size_t)i * (size_t)p.N;
+            }
+            kern<<<grid, kW2, MarchCfg::smem_bytes, s>>>(p, pl, (const P*)src, partials, status);
+        }
     } else {
         bool launched = false;
         if constexpr (kPipe) {
             if (!reread) {
-                auto kern = fused3d_kernel<kTY3, kNB, kMinB, kEarly, DD, CAL>;
+                auto kern = fused3d_kernel<kTYP, kNB, kMinB, kEarly, DD, CAL>;
                 // the dynamic shared-memory limit is a per-function attribute; setting it
                 // again is cheap and keeps this correct for every device of the process
                 cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1376,12 +1678,12 @@ cudaError_t launch_fused_cal(const KParams& p, const void* src, void* dst, doubl
                     pl.src[i] = (const P*)src + (size_t)i * (size_t)p.N;
                     pl.dst[i] = (P*)dst + (size_t)i * (size_t)p.N;
                 }
-                kern<<<grid, dim3(TX, kTY3), PipeCfg::smem_bytes, s>>>(p, pl, (const P*)src, partials, status);
+                kern<<<grid, dim3(TX, kTYP), PipeCfg::smem_bytes, s>>>(p, pl, (const P*)src, partials, status);
                 launched = true;
             }
         }
         if (!launched)
-            fused3d_reread_kernel<kTY3, CAL><<<grid, dim3(TX, kTY3), 0, s>>>(p, (const P*)src, (P*)dst, partials,
+            fused3d_reread_kernel<kTY3, CAL><<<grid3_ty3(p), dim3(TX, kTY3), 0, s>>>(p, (const P*)src, (P*)dst, partials,
                                                                               status);
     }
     return cudaGetLastError();
@@ -1400,7 +1702,7 @@ cudaError_t launch_tma_cal(const KParams& p, const void* src, void* dst, const C
             pl.src[i] = (const P*)src + (size_t)i * (size_t)p.N;
             pl.dst[i] = (P*)dst + (size_t)i * (size_t)p.N;
         }
-        kern<<<fused_grid(p), dim3(TX, kTY3), TmaCfg::smem_bytes, s>>>(p, pl, *map, (const P*)src, partials, status);
+        kern<<<grid3_ty3(p), dim3(TX, kTY3), TmaCfg::smem_bytes, s>>>(p, pl, *map, (const P*)src, partials, status);
         return cudaGetLastError();
     } else {
         return cudaErrorInvalidValue;
@@ -1414,7 +1716,7 @@ cudaError_t launch_fused_tma(const KParams& p, const void* src, void* dst, const
     const cudaError_t e = p.eos ? launch_tma_cal<kD, true>(p, src, dst, map, partials, status, s)
                                 : launch_tma_cal<kD, false>(p, src, dst, map, partials, status, s);
     ++*launches;
-    const dim3 grid = fused_grid(p);
+    const dim3 grid = grid3_ty3(p);
     *nblocks = (int)(grid.x * grid.y * grid.z);
     return e;
 }
@@ -1425,7 +1727,8 @@ cudaError_t launch_fused(const KParams& p, const void* src, void* dst, double* p
     const cudaError_t e = p.eos ? launch_fused_cal<DD, true>(p, src, dst, partials, status, s, reread)
                                 : launch_fused_cal<DD, false>(p, src, dst, partials, status, s, reread);
     ++*launches;
-    const dim3 grid = fused_grid(p);
+    const dim3 grid = DD == 2 ? ((reread || p.tile2d) ? tile2d_grid(p) : fused_grid(p))
+                              : ((reread && kPipe) ? grid3_ty3(p) : fused_grid(p));
     *nblocks = (int)(grid.x * grid.y * grid.z);
     return e;
 }
@@ -1440,10 +1743,28 @@ cudaError_t launch_fused_reread(const KParams& p, const void* src, void* dst, do
     return launch_fused<kD>(p, src, dst, partials, nblocks, status, s, launches, true);
 }
 
-// Persistent ensemble step with tile height ty (4, 8 or 16) and `grid` CTAs.
+template <bool CAL>
+cudaError_t launch_ensemble_march(const EnsembleArgs& a, const void* src, void* dst, int* status, int seg, int grid,
+                                  cudaStream_t s) {
+    auto kern = ensemble_march2d_kernel<kW2, kNBM, CAL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)MarchCfg::smem_bytes);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kW2, MarchCfg::smem_bytes, s>>>(a, (const P*)src, (P*)dst, seg, status);
+    return cudaGetLastError();
+}
+
+// Persistent ensemble step and `grid` CTAs: ty = 4, 8 or 16 runs one 32 x ty tile per work
+// unit; ty = kMarchSegs (32, 64 or 128) runs the row march over strips of kW2 nodes and
+// segments of ty rows.
 cudaError_t launch_ensemble(const EnsembleArgs& a, const void* src, void* dst, int* status, int ty, int grid,
                             cudaStream_t s, long long* launches) {
     if constexpr (kD == 2) {
+        if (ty > 16) {
+            ++*launches;
+            return a.caloric ? launch_ensemble_march<true>(a, src, dst, status, ty, grid, s)
+                             : launch_ensemble_march<false>(a, src, dst, status, ty, grid, s);
+        }
         if (a.caloric) {
             if (ty == 4) ensemble2d_kernel<4, true><<<grid, dim3(TX, 4), 0, s>>>(a, (const P*)src, (P*)dst, status);
             else if (ty == 16)
@@ -1462,11 +1783,20 @@ cudaError_t launch_ensemble(const EnsembleArgs& a, const void* src, void* dst, i
     }
 }
 
-// Occupancy (resident CTAs per SM) of the ensemble kernel with tile height ty.
+// Occupancy (resident CTAs per SM) of the ensemble kernel with tile height ty (or, above
+// 16, of the row-march form).
 int ensemble_occupancy(int ty) {
     int nb = 0;
     if constexpr (kD == 2) {
         cudaError_t e;
+        if (ty > 16) {
+            auto kern = ensemble_march2d_kernel<kW2, kNBM, false>;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg::smem_bytes) !=
+                    cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kW2, MarchCfg::smem_bytes) != cudaSuccess)
+                return 0;
+            return nb;
+        }
         // the constant-gamma form (the caloric one differs by a few registers at most)
         if (ty == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ensemble2d_kernel<4, false>, TX * 4, 0);
         else if (ty == 16)
@@ -1499,14 +1829,20 @@ template <int DD>
 int fused_occupancy_impl() {
     int n = 0;
     if constexpr (DD == 3 && kPipe) {
-        auto kern = fused3d_kernel<kTY3, kNB, kMinB, kEarly, DD, false>;
+        auto kern = fused3d_kernel<kTYP, kNB, kMinB, kEarly, DD, false>;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PipeCfg::smem_bytes) !=
                 cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX * kTY3, PipeCfg::smem_bytes) != cudaSuccess)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX * kTYP, PipeCfg::smem_bytes) != cudaSuccess)
             return 0;
     } else if constexpr (DD == 3) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused3d_reread_kernel<kTY3, false>, TX * kTY3, 0) !=
             cudaSuccess)
+            return 0;
+    } else {
+        auto kern = march2d_kernel<kW2, kNBM, false>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg::smem_bytes) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kW2, MarchCfg::smem_bytes) != cudaSuccess)
             return 0;
     }
     return n;
@@ -1516,7 +1852,7 @@ int fused_occupancy() { return fused_occupancy_impl<kD>(); }
 const Ops kOps = {kD,          kST,           sizeof(P) / 2,  sizeof(R),            max_blocks,
                   launch_init, launch_fields, launch_twopass, launch_fused_default, launch_fused_reread,
                   launch_totals, launch_ensemble, ensemble_occupancy, launch_stats,
-                  kD == 3 ? kTY3 : kTY2, fused_occupancy, launch_fused_tma, tma_supported, encode_tmap};
+                  kD == 3 ? (kPipe ? kTYP : kTY3) : 1, fused_occupancy, launch_fused_tma, tma_supported, encode_tmap};
 
 }  // namespace
 

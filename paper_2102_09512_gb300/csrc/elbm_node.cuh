@@ -30,7 +30,9 @@ struct KParams {
     double gm1;                  // gamma - 1  (so Cv = 1 / gm1)
     double Pr, mu0, T0, mu_exp;
     int deriv;                   // 0 upwind, 1 central
-    int tz;                      // z-segment length of the fused 3D kernels
+    int tz;                      // segment length of the fused kernels (D3Q27: z planes, D2Q9: rows)
+    int tile2d;                  // D2Q9: the default fused schedule runs the one-tile-per-CTA kernel
+                                 // (grids whose row march would not fill the device)
     float2 rest2[27];            // rest-state pair (f_i, g_i) of every direction, deviation stores
     float rest_rho, rest_Pxx, rest_Pyy, rest_Pzz, rest_E;   // their moment sums
     // The same parameters precomputed in both arithmetic types, so that no kernel

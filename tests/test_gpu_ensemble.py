@@ -37,6 +37,7 @@ def small_cases():
     caloric.cv = (1.0, 4.0, -4.0, 5.0)   # a cubic Cv(T) instance among constant-gamma ones
     return [
         C.random_smooth(2, 45, 23, 1, seed=1, mu0=0.01),
+        C.random_smooth(2, 200, 37, 1, seed=4, mu0=0.01),   # two row-march strips, the second ragged
         C.sod(nx=64, ny=9, mu=0.015),
         C.random_smooth(2, 37, 29, 1, seed=2, mu0=0.02, bc=(1, 1, 1, 1, 0, 0)),
         C.shock_vortex(nx=96, ny=40, r_v=5.0, Ma_s=1.3, inflow=True),   # fixed-state -x face
@@ -65,10 +66,15 @@ def test_instances_match_single_lattice_runs(E, store):
     ens.close()
 
 
-@pytest.mark.parametrize("mode,graph,tile_y,ctas", [(0, True, 4, 3), (0, False, 16, 1), (1, False, 8, 1)])
+@pytest.mark.parametrize("mode,graph,tile_y,ctas", [(0, True, 4, 3), (0, False, 16, 1), (1, False, 8, 1),
+                                                    (0, True, 32, 2), (0, False, 64, 1), (0, True, 128, 4)])
 def test_schedules_agree(E, mode, graph, tile_y, ctas):
+    """tile_y 4/8/16: one tile per work unit; 32/64/128: row-march segments of that many
+    rows.  15 steps: one graph of 8 steps and 7 one-step graphs in the graph modes."""
     cs = small_cases()
     ref = E.Ensemble.from_cases(cs, store="f32")
+    ref.set_mode(0, False)
+    ref.set_schedule(8, 1)
     ref.step(15)
     ens = E.Ensemble.from_cases(cs, store="f32")
     ens.set_mode(mode, graph)
@@ -87,7 +93,7 @@ def test_tuner_keeps_state_and_picks_a_valid_schedule(E):
     ens.step(3)
     before = [ens.fields(k) for k in range(len(cs))]
     ty, ctas, grid = ens.tune(trial_steps=2)
-    assert ty in (4, 8, 16) and ctas >= 1 and grid >= 1
+    assert ty in (4, 8, 16, 32, 64, 128) and ctas >= 1 and grid >= 1
     after = [ens.fields(k) for k in range(len(cs))]
     for b, a in zip(before, after):
         for x, y in zip(b, a):
@@ -102,11 +108,32 @@ def test_tuner_keeps_state_and_picks_a_valid_schedule(E):
     ref.close()
 
 
-def test_instance_matches_oracle(E):
+def test_multi_step_graph_matches_single_launches(E):
+    """Steps replayed from the 8-step graph equal steps launched one at a time, bit for
+    bit (the same kernels on the same stores, in the same order)."""
+    cs = small_cases()
+    a = E.Ensemble.from_cases(cs, store="f32")
+    a.set_mode(0, True)
+    a.step(17)
+    b = E.Ensemble.from_cases(cs, store="f32")
+    b.set_mode(0, False)
+    b.set_schedule(*a.schedule()[:2])
+    for _ in range(17):
+        b.step(1)
+    for k in range(len(cs)):
+        for x, y in zip(a.fields(k), b.fields(k)):
+            assert np.array_equal(x, y), k
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("tile_y", [8, 64])
+def test_instance_matches_oracle(E, tile_y):
     cs = small_cases()
     ens = E.Ensemble.from_cases(cs, store="f64")
+    ens.set_schedule(tile_y, 2)
     ens.step(25)
-    for k in (1, 3, 4):
+    for k in (1, 2, 4, 5):
         c = cs[k]
         p = O.Params(D=2, nx=c.nx, ny=c.ny, nz=1, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0, mu_exp=c.mu_exp,
                      bc=c.bc, fixed=c.fixed, cv=c.cv)
