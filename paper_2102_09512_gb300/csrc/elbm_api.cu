@@ -246,6 +246,9 @@ int elbm_step(elbm_handle* h, int nsteps) {
             e = h->ops->step_fused_tma(h->kp, src, dst, &h->tmap[h->cur], step_partials(h), &h->step_blocks,
                                        status_ptr(h), h->stream, &h->launches);
         }
+        else if (h->tmap_ready)
+            e = h->ops->step_fused_pf(h->kp, src, dst, &h->tmap[h->cur], step_partials(h), &h->step_blocks,
+                                      status_ptr(h), h->stream, &h->launches);
         else
             e = h->ops->step_fused(h->kp, src, dst, step_partials(h), &h->step_blocks, status_ptr(h), h->stream,
                                    &h->launches);

@@ -203,7 +203,10 @@ inline NoallocLayout noalloc_layout(long long N, int D, size_t real_bytes) {
 // D2Q9 row march: a CTA owns a strip of kMarchW2 nodes of a row and marches along y;
 // the persistent ensemble runs it with segments of one of kMarchSegs rows (a schedule
 // value above 16; 4, 8 and 16 select the one-tile-per-unit kernel with 32 x ty tiles).
-constexpr int kMarchW2 = 128;
+#ifndef ELBM_MARCH_W
+#define ELBM_MARCH_W 128
+#endif
+constexpr int kMarchW2 = ELBM_MARCH_W;
 constexpr int kMarchSegs[3] = {32, 64, 128};
 
 // Layout of the auxiliary buffer (all offsets 256-byte aligned).
@@ -270,6 +273,9 @@ struct Ops {
     int (*tma_supported)(const KParams& p);   // the grid suits the TMA-staged D3Q27 kernel
     // tensor map of a store for that kernel: 1 made, 0 not applicable, -1 the driver refused
     int (*encode_tmap)(const KParams& p, const void* base, CUtensorMap* out);
+    // the default fused step given src's tensor map (L2 prefetch of the planes ahead)
+    cudaError_t (*step_fused_pf)(const KParams& p, const void* src, void* dst, const CUtensorMap* src_map,
+                                 double* partials, int* nblocks, int* status, cudaStream_t s, long long* launches);
 };
 
 // z-segment length of the fused D3Q27 kernels.  Each CTA marches one (tile, segment)

@@ -23,6 +23,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <type_traits>
 
 #include "elbm_internal.h"
@@ -713,10 +714,31 @@ struct PipeBytes {
     static constexpr size_t value = Pipe<TY, NB>::smem_bytes;
 };
 
+// Store of a post-collision pair.  With ELBM_STCS the store is marked streaming (evict
+// first), so that the step's writes do not push the planes prefetched ahead out of L2.
+#ifndef ELBM_STCS
+#define ELBM_STCS 1
+#endif
+__device__ __forceinline__ void store_pair(P* ptr, P v) {
+    if constexpr (ELBM_STCS && sizeof(P) <= 8) __stcs(ptr, v);
+    else *ptr = v;
+}
+
+// L2 prefetch of one box of a direction plane through the tensor-copy unit (no shared
+// memory, no L1; a hint: boxes that leave the tensor are clipped).  x * element size
+// must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, int y, int w) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];\n" ::"l"(
+                     reinterpret_cast<unsigned long long>(map)),
+                 "r"(x), "r"(y), "r"(w)
+                 : "memory");
+}
+
 template <int TY, int NB, int MINB, bool EARLY, int DD, bool CAL>
 __global__ void __launch_bounds__(TX * TY, MINB)
 fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPlanes pl,
-               const P* __restrict__ src, double* __restrict__ partials, int* __restrict__ status) {
+               const P* __restrict__ src, double* __restrict__ partials, int* __restrict__ status,
+               const __grid_constant__ CUtensorMap pmap, int pref) {
     using PP = Pipe<TY, NB>;
     static_assert(NB == 2, "plane z+2 is prefetched into the slots of plane z");
     static_assert(sizeof(R) == 4 && DD == 3, "the pipelined kernel is D3Q27 in FP32");
@@ -771,6 +793,21 @@ fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPla
     };
     using Full = std::true_type;
     using Lite = std::false_type;
+    // pref > 0: plane q's pulled source windows are prefetched into L2 `pref` planes
+    // before their cp.async copies are issued (one tensor-prefetch box per direction,
+    // issued by lanes of the last warp, which has no halo work), so that the copies of
+    // the plane buffer find their lines in L2.  The box for direction i covers the
+    // columns x0 - XO .. x0 + TX + XO - 1 (XO keeps its first column 16-byte aligned)
+    // and rows y0 - 1 - c_y .. y0 + TY - c_y of source plane q - c_z.
+    constexpr int XO = 16 / (int)sizeof(P);
+    const int pf_lane = tid - (NT - 32);
+    auto prefetch_plane = [&](int q) {
+        if (pf_lane >= 0 && pf_lane < Q) {
+            const int i = pf_lane, b = (i / 3) % 3, c = i / 9;
+            // starts clamped to the tensor (x0 - XO stays a multiple of XO)
+            tma_prefetch_3d(&pmap, max(x0 - XO, 0), max(y0 - b, 0), i * p.nz + map_axis(q + 1 - c, p.nz, p.per_z));
+        }
+    };
 
     Acc5 acc;
     acc.zero();
@@ -779,6 +816,7 @@ fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPla
     // prologue: Q~_zzz below the segment, planes zb and zb+1 in flight, moments of zb
     R qz_prev = R(0), qz_cur = R(0), qz_next = R(0);
     if (active) qz_prev = direct_anomaly_z<CAL>(p, src, x, y, map_axis(zb - 1, p.nz, p.per_z));
+    for (int d = 2; d < 2 + pref && zb + d <= ze; ++d) prefetch_plane(map_axis(zb + d, p.nz, p.per_z));
     issue_plane(zb, 0, true);
     issue_plane(map_axis(zb + 1, p.nz, p.per_z), 1 % NB, zb + 1 < ze);
     Moments<R> m_cur, m_next;
@@ -810,6 +848,7 @@ fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPla
         // moments of plane z+1, so the copy overlaps them too (both planes are live
         // in registers meanwhile, which only a one-CTA-per-SM launch affords)
         P pk[Q];   // the pulled pairs of plane z, as stored
+        if (pref > 0 && z + 2 + pref <= ze) prefetch_plane(map_axis(z + 2 + pref, p.nz, p.per_z));
         if (EARLY) {
             if (active) {
                 const P* bb = buf + (size_t)sz * Q * NS + tid;
@@ -858,7 +897,7 @@ fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPla
             for (int i = 0; i < Q; ++i) {
                 R f, g;
                 Cd::dec(pk[i], f, g);
-                pl.dst[i][n] = Cd::enc(rx.f(i, f, p), rx.g(i, g, p));
+                store_pair(pl.dst[i] + n, Cd::enc(rx.f(i, f, p), rx.g(i, g, p)));
             }
         }
         m_cur = m_next;
@@ -1643,9 +1682,14 @@ cudaError_t launch_twopass(const KParams& p, const void* src, void* dst, void* q
 
 // A template so that the branch of the other lattice is never instantiated; CAL as in
 // the kernels (the caloric form only for handles with a Cv(T) model).
+#ifndef ELBM_PREF
+#define ELBM_PREF 1
+#endif
+constexpr int kPref = ELBM_PREF;   // planes of L2 prefetch ahead of the cp.async copies (with a tensor map)
+
 template <int DD, bool CAL>
 cudaError_t launch_fused_cal(const KParams& p, const void* src, void* dst, double* partials, int* status,
-                             cudaStream_t s, bool reread) {
+                             cudaStream_t s, bool reread, const CUtensorMap* pmap = nullptr) {
     const dim3 grid = fused_grid(p);
     if constexpr (DD == 2) {
         if (reread || p.tile2d) {   // the tile kernel: one 32 x kTY2 tile per CTA, no march
@@ -1678,7 +1722,10 @@ cudaError_t launch_fused_cal(const KParams& p, const void* src, void* dst, doubl
                     pl.src[i] = (const P*)src + (size_t)i * (size_t)p.N;
                     pl.dst[i] = (P*)dst + (size_t)i * (size_t)p.N;
                 }
-                kern<<<grid, dim3(TX, kTYP), PipeCfg::smem_bytes, s>>>(p, pl, (const P*)src, partials, status);
+                CUtensorMap none;
+                std::memset(&none, 0, sizeof(none));
+                kern<<<grid, dim3(TX, kTYP), PipeCfg::smem_bytes, s>>>(p, pl, (const P*)src, partials, status,
+                                                                       pmap ? *pmap : none, pmap ? kPref : 0);
                 launched = true;
             }
         }
@@ -1723,9 +1770,10 @@ cudaError_t launch_fused_tma(const KParams& p, const void* src, void* dst, const
 
 template <int DD>
 cudaError_t launch_fused(const KParams& p, const void* src, void* dst, double* partials, int* nblocks,
-                         int* status, cudaStream_t s, long long* launches, bool reread) {
-    const cudaError_t e = p.eos ? launch_fused_cal<DD, true>(p, src, dst, partials, status, s, reread)
-                                : launch_fused_cal<DD, false>(p, src, dst, partials, status, s, reread);
+                         int* status, cudaStream_t s, long long* launches, bool reread,
+                         const CUtensorMap* pmap = nullptr) {
+    const cudaError_t e = p.eos ? launch_fused_cal<DD, true>(p, src, dst, partials, status, s, reread, pmap)
+                                : launch_fused_cal<DD, false>(p, src, dst, partials, status, s, reread, pmap);
     ++*launches;
     const dim3 grid = DD == 2 ? ((reread || p.tile2d) ? tile2d_grid(p) : fused_grid(p))
                               : ((reread && kPipe) ? grid3_ty3(p) : fused_grid(p));
@@ -1741,6 +1789,12 @@ cudaError_t launch_fused_default(const KParams& p, const void* src, void* dst, d
 cudaError_t launch_fused_reread(const KParams& p, const void* src, void* dst, double* partials, int* nblocks,
                                 int* status, cudaStream_t s, long long* launches) {
     return launch_fused<kD>(p, src, dst, partials, nblocks, status, s, launches, true);
+}
+
+// The default fused step with src's tensor map at hand (L2 prefetch of the planes ahead).
+cudaError_t launch_fused_pf(const KParams& p, const void* src, void* dst, const CUtensorMap* map, double* partials,
+                            int* nblocks, int* status, cudaStream_t s, long long* launches) {
+    return launch_fused<kD>(p, src, dst, partials, nblocks, status, s, launches, false, map);
 }
 
 template <bool CAL>
@@ -1852,7 +1906,8 @@ int fused_occupancy() { return fused_occupancy_impl<kD>(); }
 const Ops kOps = {kD,          kST,           sizeof(P) / 2,  sizeof(R),            max_blocks,
                   launch_init, launch_fields, launch_twopass, launch_fused_default, launch_fused_reread,
                   launch_totals, launch_ensemble, ensemble_occupancy, launch_stats,
-                  kD == 3 ? (kPipe ? kTYP : kTY3) : 1, fused_occupancy, launch_fused_tma, tma_supported, encode_tmap};
+                  kD == 3 ? (kPipe ? kTYP : kTY3) : 1, fused_occupancy, launch_fused_tma, tma_supported, encode_tmap,
+                  launch_fused_pf};
 
 }  // namespace
 
