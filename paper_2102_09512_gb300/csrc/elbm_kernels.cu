@@ -1009,6 +1009,11 @@ struct Tma {
 // executes fewer instructions and waits far less at the plane barrier, but the boxes
 // carry 11-19 % more pairs than the pulls use (corners, and the columns that keep the
 // box 16-byte aligned) and the kernel draws 12-25 % more DRAM reads.
+#ifndef ELBM_PREF_TMA
+#define ELBM_PREF_TMA 0   // measured: FP32 11.16 -> 10.95 GLUPS with it at 256^3, FP16 19.3 -> 19.5
+#endif
+constexpr bool kPrefTma = ELBM_PREF_TMA;
+
 template <int TY, int MINB, int DD, bool CAL>
 __global__ void __launch_bounds__(TX * TY, MINB)
 fused3d_tma_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPlanes pl,
@@ -1109,6 +1114,16 @@ fused3d_tma_kernel(const __grid_constant__ KParams p, const __grid_constant__ Di
     // prologue: Q~_zzz below the segment, planes zb and zb+1 in flight, moments of zb
     R qz_prev = R(0), qz_cur = R(0), qz_next = R(0);
     if (active) qz_prev = direct_anomaly_z<CAL>(p, src, x, y, map_axis(zb - 1, p.nz, p.per_z));
+    // L2 prefetch of the plane after the two in flight (as in fused3d_kernel), by lanes of
+    // the last warp
+    const int pf_lane = tid - (NT - 32);
+    auto prefetch_plane = [&](int q) {
+        if (kPrefTma && pf_lane >= 0 && pf_lane < Q) {
+            const int i = pf_lane, b = (i / 3) % 3, c = i / 9;
+            tma_prefetch_3d(&tmap, max(x0 - XO, 0), max(y0 - b, 0), i * p.nz + map_axis(q + 1 - c, p.nz, p.per_z));
+        }
+    };
+    if (zb + 2 <= ze) prefetch_plane(map_axis(zb + 2, p.nz, p.per_z));
     issue_plane(zb, 0);
     issue_plane(map_axis(zb + 1, p.nz, p.per_z), 1);
     Moments<R> m_cur, m_next;
@@ -1142,6 +1157,7 @@ fused3d_tma_kernel(const __grid_constant__ KParams p, const __grid_constant__ Di
             gave_up = true;
             break;
         }
+        if (z + 3 <= ze) prefetch_plane(map_axis(z + 3, p.nz, p.per_z));
         if (z + 2 <= ze) issue_plane(map_axis(z + 2, p.nz, p.per_z), sz);
 
         if (active) {
@@ -1612,9 +1628,12 @@ int encode_tmap(const KParams& p, const void* base, CUtensorMap* out) {
     const cuuint32_t box[3] = {(cuuint32_t)TmaCfg::BW, (cuuint32_t)TmaCfg::RB, 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     const CUtensorMapDataType dt = sizeof(P) == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+#ifndef ELBM_TMAP_PROMO
+#define ELBM_TMAP_PROMO CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+#endif
     const CUresult r = encode(out, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                              (CUtensorMapL2promotion)ELBM_TMAP_PROMO, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 1 : -1;
 }
 

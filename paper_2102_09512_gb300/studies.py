@@ -194,3 +194,40 @@ def precision_study(n: int = 256, steps: int = 100, stores=("f32", "f16dev", "bf
         torch.cuda.empty_cache()
         out[store] = e
     return out
+
+
+def _turbulence_report(out: dict, fit=(6, 16)) -> dict:
+    """Histories of a decaying_turbulence run relative to their initial values, and the
+    spectral slope fitted over integer shells fit[0] .. fit[1] at each spectrum time."""
+    h = out["hist"]
+    K0 = h[0]["K"]
+    rows = [dict(t_star=s["t_star"], K_over_K0=s["K"] / K0, dissipation=s["dissipation"],
+                 Re_lambda=s["Re_lambda"], theta_rms=s["theta_rms"], rho_rms=s["rho_rms"], Ma_t=s["Ma_t"])
+            for s in h]
+    slopes = {}
+    for ts, (k, Ek) in out["spectra"].items():
+        sel = (k >= fit[0]) & (k <= fit[1]) & (Ek > 0)
+        slopes[ts] = float(np.polyfit(np.log(k[sel]), np.log(Ek[sel]), 1)[0])
+        peak = int(k[1:][np.argmax(Ek[1:])])
+        slopes[f"peak_shell_t{ts}"] = peak
+    return dict(n=out["n"], tau_steps=out["tau"], steps=out["steps"], step_seconds=out["step_seconds"],
+                mu0=out["mu0"], glups=out["n"] ** 3 * out["steps"] / max(out["step_seconds"], 1e-9) / 1e9,
+                history=rows, spectral_slopes=slopes, fit_shells=list(fit))
+
+
+if __name__ == "__main__":
+    # python -m paper_2102_09512_gb300.studies decaying_turbulence N [out.json]
+    #   decaying compressible turbulence on an N^3 box (Sec. III.D; N = 768 is the paper's
+    #   Re_lambda = 175, Ma_t = 0.488 run), FP32 store, statistics every tau/4 to t* = 3,
+    #   spectra at t* = 0, 1, 3; prints (and writes) the histories and spectral slopes.
+    import json
+    import sys
+
+    if len(sys.argv) < 3 or sys.argv[1] != "decaying_turbulence":
+        raise SystemExit("usage: python -m paper_2102_09512_gb300.studies decaying_turbulence N [out.json]")
+    rep = _turbulence_report(decaying_turbulence(n=int(sys.argv[2])))
+    txt = json.dumps(rep, indent=1)
+    print(txt)
+    if len(sys.argv) > 3:
+        with open(sys.argv[3], "w") as fh:
+            fh.write(txt)
