@@ -529,6 +529,25 @@ struct Relax {
         if constexpr (DEV) t = fma(-w, R(p.rest2[i].x), t);
         return fma(omw, fi, t);
     }
+    // Both updates of direction i at once, as two-lane FP32 arithmetic (FFMA2, sm_100 and
+    // later): the same operations in the same order as f() and g(), so the same results.
+    __device__ __forceinline__ float2 fg(int i, float2 v, const KParams& p) const {
+        static_assert(sizeof(R) == 4, "two-lane form of the FP32 arithmetic");
+        const int a = cx_of(i) + 1, b = cy_of(i) + 1, c = (D == 3) ? cz_of<D>(i) + 1 : 1;
+        const R yz = wr * Y[b] * Z[c];
+        const R A = w1r * gy[b] * gz[c];
+        const R B = w1r * (sy[b] * gz[c] + gy[b] * sz[c]);
+        float2 t = make_float2(X[a] * yz, fma(ax[a], A, gx[a] * B));
+        if constexpr (DEV) t = __ffma2_rn(make_float2(-w, -w1), p.rest2[i], t);
+        float2 o = __ffma2_rn(make_float2(omw, omw1), v, t);
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of<D>(i);
+        if (cx * cx + cy * cy + cz * cz == 1) {
+            const R q = cx != 0 ? dq[0] : (cy != 0 ? dq[1] : dq[2]);
+            if (cx + cy + cz < 0) o.y += h * q;
+            else o.y -= h * q;
+        }
+        return o;
+    }
     __device__ __forceinline__ R g(int i, R gi, const KParams& p) const {
         constexpr int Q = Lat<D>::Q;
         const int a = cx_of(i) + 1, b = cy_of(i) + 1, c = (D == 3) ? cz_of<D>(i) + 1 : 1;

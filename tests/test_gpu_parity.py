@@ -177,6 +177,25 @@ def test_d3q27_parity_100_steps(E, case, store, kernel):
     assert_parity(gpu_fields(E, c, steps, store, kernel, tz=tz), ref, TOL[store], (case, kernel, store))
 
 
+INNER_3D = {
+    # tiles of 32 x 8 with two nodes of margin to every x and y face (x0 = 32, 64; y0 = 8, 16):
+    # their pull addresses skip the boundary maps on the planes away from the z faces
+    "periodic": lambda: C.random_smooth(3, 100, 30, 12, seed=131, mu0=0.01, du=0.05, u0=U0_3D),
+    "zerograd": lambda: C.random_smooth(3, 100, 30, 12, seed=132, mu0=0.01, du=0.05, u0=U0_3D,
+                                        bc=(1, 1, 1, 1, 1, 1)),
+}
+
+
+@pytest.mark.parametrize("kernel", [0, 3])
+@pytest.mark.parametrize("case,store", [(c, s) for c in INNER_3D for s in ("f64", "f32", "f16dev")])
+def test_d3q27_inner_tiles(E, case, store, kernel):
+    if kernel == 3 and store == "f64":
+        pytest.skip("the tensor-copy schedule runs the FP32-arithmetic stores only")
+    c = INNER_3D[case]()
+    ref = oracle_fields(("inner", case), c, 60)
+    assert_parity(gpu_fields(E, c, 60, store, kernel), ref, TOL[store], (case, store, kernel))
+
+
 @pytest.mark.parametrize("store", ["f64", "f32", "f16dev"])
 @pytest.mark.parametrize("tz", [1, 2, 5, 7, 64])
 def test_d3q27_z_segments(E, tz, store):
