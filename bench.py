@@ -240,11 +240,11 @@ def run_reference(args):
     return 0
 
 
-def time_store(E, torch, case, store, steps, warmup, stream, kernel=0, windows=1):
+def time_store(E, torch, case, store, steps, warmup, stream, kernel=0, windows=1, layout=0):
     """Device-resident timing: `windows` back-to-back windows of `steps` steps each (CUDA
     events on the launching stream, a synchronize on both sides of every window); returns
     (ms_per_step of each window, launches per window, solver, status)."""
-    g = E.Solver.from_case(case, store=store, stream=stream)
+    g = E.Solver.from_case(case, store=store, stream=stream, layout=layout)
     g.set_kernel(kernel)
     for w in range(warmup):
         g.step(1)
@@ -341,6 +341,30 @@ def d2q9_measure(E, torch, steps, warmup=3, side=4096):
     return out
 
 
+def aa_measure(E, torch, case, steps, warmup=3):
+    """The single-store (AA) layout on the bench workload: the two-pass schedule updating one
+    store in place (half the population memory), against the two-pass schedule on ping-pong
+    stores; GLUPS and the fraction of the measured HBM peak at the two-pass bytes per update
+    (the populations read twice and written once, plus the Q~ field)."""
+    peak, _ = _peak_hbm()
+    out = {"grid": [case.nx, case.ny, case.nz], "steps": steps, "schedule": "two-pass"}
+    for store in ("f32", "f16dev"):
+        for name, layout in (("aa", 1), ("pingpong", 0)):
+            try:
+                ms, _, g, _ = time_store(E, torch, case, store, steps, warmup, torch.cuda.current_stream(),
+                                         KERNELS["twopass"], 1, layout)
+                g.close()
+            except E.ElbmError as err:
+                out[f"{store}_{name}"] = {"error": str(err)}
+                continue
+            glups = case.N / (ms[0] * 1e-3) / 1e9
+            nbytes = 3 * BYTES_PER_UPDATE[store] // 2 + 3 * 4 * 2   # pairs read twice, written once; Q~ out and in
+            out[f"{store}_{name}"] = {"glups": glups, "ms_per_step": ms[0], "hbm_frac": glups * nbytes / peak,
+                                      "bytes_per_update": nbytes}
+        torch.cuda.empty_cache()
+    return out
+
+
 ENSEMBLE_MAX_STEPS = 50   # timed steps per ensemble phase (see ensemble_measure)
 
 
@@ -406,6 +430,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-d2q9", action="store_true")
+    ap.add_argument("--no-aa", action="store_true")
     ap.add_argument("--windows", type=int, default=5,
                     help="back-to-back timed windows of --steps steps for the headline store (median reported)")
     ap.add_argument("--size", type=int, default=N_SIDE, help="box side (the bench workload is 256)")
@@ -525,6 +550,10 @@ def main():
     if not args.no_d2q9:
         d2q9 = d2q9_measure(E, torch, args.steps)
 
+    aa = None
+    if not args.no_aa:
+        aa = aa_measure(E, torch, case, args.steps)
+
     ens = None
     if not args.no_ensemble:
         ens = ensemble_measure(E, torch, args.steps)
@@ -554,7 +583,7 @@ def main():
                    "schedule": args.kernel, "l2": "inputs larger than L2 (3.6 GB FP32 store)",
                    "parallelism": "replicas" if ws > 1 else "single-gpu"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_head,
-        "clocks": clocks, "variants": variants, "ensemble": ens, "d2q9": d2q9,
+        "clocks": clocks, "variants": variants, "ensemble": ens, "d2q9": d2q9, "aa_layout": aa,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:

@@ -29,6 +29,7 @@ struct elbm_handle {
     bool bound;
     int cur;                 // index of the store holding the current state
     int kernel;              // elbm_kernel
+    int layout;              // elbm_layout
     int step_blocks;         // CTAs that wrote step partials in the last step
     long long steps;
     long long launches;
@@ -38,6 +39,9 @@ namespace {
 
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+// Host field transfers of an AA handle go through the staging area in chunks of this many
+// nodes (a ping-pong handle stages the whole grid at once).
+constexpr long long kStagingChunk = 1LL << 25;
 
 const Ops* pick_ops(int D, int store) {
     if (D == 2) {
@@ -89,6 +93,37 @@ __global__ void finalize_kernel(const double* __restrict__ partials, int nb, int
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? ELBM_OK : ELBM_ERR_CUDA; }
+
+// Nodes staged per host field transfer.
+long long staging_nodes(const elbm_handle* h) {
+    return h->layout == ELBM_LAYOUT_AA && h->N > kStagingChunk ? kStagingChunk : h->N;
+}
+
+// Layout of the auxiliary buffer (all offsets 256-byte aligned).
+void compute_aux(elbm_handle* h) {
+    AuxLayout& a = h->aux;
+    a.max_blocks = h->ops->max_blocks(h->kp);
+    size_t off = 0;
+    a.status = off;
+    off = align_up(off + sizeof(int));
+    a.totals = off;
+    off = align_up(off + kMaxWidth * sizeof(double));
+    a.partials = off;
+    off = align_up(off + (5 + kStatsSums) * sizeof(double) * (size_t)a.max_blocks);
+    a.qfield = off;
+    off = align_up(off + (size_t)h->D * (size_t)h->N * h->ops->real_bytes);
+    a.staging = off;
+    off = align_up(off + (size_t)5 * (size_t)staging_nodes(h) * sizeof(double));
+    a.bytes = off;
+}
+
+// Kernel parameters for the diagnostics: how the current state C(X_n) is laid out in the
+// store (in place, or the AA layout of the step parity).
+KParams diag_params(const elbm_handle* h) {
+    KParams k = h->kp;
+    k.aa = h->layout == ELBM_LAYOUT_AA ? (h->steps % 2 == 0 ? 1 : 2) : 0;
+    return k;
+}
 
 int* status_ptr(elbm_handle* h) { return (int*)(h->auxp + h->aux.status); }
 double* totals_ptr(elbm_handle* h) { return (double*)(h->auxp + h->aux.totals); }
@@ -147,6 +182,7 @@ int elbm_create(const elbm_params* prm, elbm_handle** out) {
     h->N = N;
     h->ops = pick_ops(D, p.store);
     h->kernel = ELBM_KERNEL_FUSED;
+    h->layout = ELBM_LAYOUT_PINGPONG;
 
     h->kp = kp;
     {
@@ -165,20 +201,7 @@ int elbm_create(const elbm_params* prm, elbm_handle** out) {
     const KParams& k = h->kp;
 
     h->pop_bytes = (size_t)2 * h->Q * (size_t)N * h->ops->value_bytes;
-    AuxLayout& a = h->aux;
-    a.max_blocks = h->ops->max_blocks(k);
-    size_t off = 0;
-    a.status = off;
-    off = align_up(off + sizeof(int));
-    a.totals = off;
-    off = align_up(off + kMaxWidth * sizeof(double));
-    a.partials = off;
-    off = align_up(off + (5 + kStatsSums) * sizeof(double) * (size_t)a.max_blocks);
-    a.qfield = off;
-    off = align_up(off + (size_t)D * N * h->ops->real_bytes);
-    a.staging = off;
-    off = align_up(off + (size_t)5 * N * sizeof(double));
-    a.bytes = off;
+    compute_aux(h);
     *out = h;
     return ELBM_OK;
 }
@@ -191,12 +214,19 @@ int elbm_bytes_required(const elbm_handle* h, size_t* pop_bytes, size_t* aux_byt
 }
 
 int elbm_bind(elbm_handle* h, void* pop_a, void* pop_b, void* aux, void* stream) {
-    if (!h || !pop_a || !pop_b || !aux || pop_a == pop_b) return ELBM_ERR_ARG;
+    if (!h || !pop_a || !aux) return ELBM_ERR_ARG;
+    const bool aa = h->layout == ELBM_LAYOUT_AA;
+    if (aa) {
+        if (pop_b && pop_b != pop_a) return ELBM_ERR_ARG;   // one store
+        pop_b = pop_a;
+    } else if (!pop_b || pop_a == pop_b) {
+        return ELBM_ERR_ARG;
+    }
     if (((uintptr_t)pop_a | (uintptr_t)pop_b | (uintptr_t)aux) % kAlign) return ELBM_ERR_ARG;
     h->pop[0] = pop_a;
     h->pop[1] = pop_b;
     h->tmap_ready = false;
-    if (h->ops->tma_supported(h->kp))
+    if (!aa && h->ops->tma_supported(h->kp))
         h->tmap_ready = h->ops->encode_tmap(h->kp, pop_a, &h->tmap[0]) == 1 &&
                         h->ops->encode_tmap(h->kp, pop_b, &h->tmap[1]) == 1;
     h->auxp = (char*)aux;
@@ -206,16 +236,51 @@ int elbm_bind(elbm_handle* h, void* pop_a, void* pop_b, void* aux, void* stream)
     return cuda_status(cudaMemsetAsync(status_ptr(h), 0, sizeof(int), h->stream));
 }
 
+// AA: C(X_0) in layout L0 from equilibria already written in place (a step from layout L1
+// collides them without streaming).
+int aa_collide_initial(elbm_handle* h) {
+    int nb = 0;
+    return cuda_status(h->ops->step_aa(h->kp, h->pop[0], h->auxp + h->aux.qfield, query_partials(h), &nb,
+                                       status_ptr(h), h->stream, &h->launches, 1));
+}
+
 int elbm_set_fields_device(elbm_handle* h, const double* rho, const double* u, const double* T) {
     if (!h || !h->bound || !rho || !u || !T) return ELBM_ERR_ARG;
     h->cur = 0;
     h->steps = 0;
+    if (h->layout == ELBM_LAYOUT_AA) {
+        const int rc = cuda_status(h->ops->init_nodes(h->kp, rho, u, T, h->pop[0], 0, h->N, status_ptr(h),
+                                                      h->stream, &h->launches));
+        return rc != ELBM_OK ? rc : aa_collide_initial(h);
+    }
     return cuda_status(h->ops->init(h->kp, rho, u, T, h->pop[0], h->pop[1], h->auxp + h->aux.qfield,
                                     query_partials(h), status_ptr(h), h->stream, &h->launches));
 }
 
 int elbm_set_fields(elbm_handle* h, const double* rho, const double* u, const double* T) {
     if (!h || !h->bound || !rho || !u || !T) return ELBM_ERR_ARG;
+    if (h->layout == ELBM_LAYOUT_AA) {   // chunks of staging_nodes(h) nodes
+        h->cur = 0;
+        h->steps = 0;
+        const long long N = h->N, C = staging_nodes(h);
+        double* st = staging(h);
+        for (long long n0 = 0; n0 < N; n0 += C) {
+            const long long c = N - n0 < C ? N - n0 : C;
+            cudaError_t e = cudaMemcpyAsync(st, rho + n0, c * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+            for (int d = 0; d < h->D && e == cudaSuccess; ++d)
+                e = cudaMemcpyAsync(st + (1 + d) * c, u + d * N + n0, c * sizeof(double), cudaMemcpyHostToDevice,
+                                    h->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(st + (1 + h->D) * c, T + n0, c * sizeof(double), cudaMemcpyHostToDevice,
+                                    h->stream);
+            if (e == cudaSuccess)
+                e = h->ops->init_nodes(h->kp, st, st + c, st + (1 + h->D) * c, h->pop[0], n0, c, status_ptr(h),
+                                       h->stream, &h->launches);
+            if (e != cudaSuccess) return ELBM_ERR_CUDA;
+        }
+        const int rc = aa_collide_initial(h);
+        return rc != ELBM_OK ? rc : sync_status(h);
+    }
     const size_t N = (size_t)h->N;
     double* st = staging(h);
     cudaError_t e = cudaMemcpyAsync(st, rho, N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
@@ -231,6 +296,16 @@ int elbm_set_fields(elbm_handle* h, const double* rho, const double* u, const do
 
 int elbm_step(elbm_handle* h, int nsteps) {
     if (!h || !h->bound || nsteps < 0) return ELBM_ERR_ARG;
+    if (h->layout == ELBM_LAYOUT_AA) {   // the layout alternates: L0 after an even number of steps
+        for (int s = 0; s < nsteps; ++s) {
+            const cudaError_t e = h->ops->step_aa(h->kp, h->pop[0], h->auxp + h->aux.qfield, step_partials(h),
+                                                  &h->step_blocks, status_ptr(h), h->stream, &h->launches,
+                                                  (int)(h->steps % 2));
+            if (e != cudaSuccess) return ELBM_ERR_CUDA;
+            ++h->steps;
+        }
+        return ELBM_OK;
+    }
     for (int s = 0; s < nsteps; ++s) {
         const void* src = h->pop[h->cur];
         void* dst = h->pop[1 - h->cur];
@@ -261,11 +336,33 @@ int elbm_step(elbm_handle* h, int nsteps) {
 
 int elbm_get_fields_device(elbm_handle* h, double* rho, double* u, double* T) {
     if (!h || !h->bound || !rho || !u || !T) return ELBM_ERR_ARG;
-    return cuda_status(h->ops->fields(h->kp, h->pop[h->cur], rho, u, T, status_ptr(h), h->stream, &h->launches));
+    return cuda_status(h->ops->fields(diag_params(h), h->pop[h->cur], rho, u, T, status_ptr(h), h->stream,
+                                      &h->launches));
 }
 
 int elbm_get_fields(elbm_handle* h, double* rho, double* u, double* T) {
     if (!h || !h->bound || !rho || !u || !T) return ELBM_ERR_ARG;
+    if (h->layout == ELBM_LAYOUT_AA) {   // chunks of staging_nodes(h) nodes
+        const long long N = h->N, C = staging_nodes(h);
+        const KParams k = diag_params(h);
+        double* st = staging(h);
+        for (long long n0 = 0; n0 < N; n0 += C) {
+            const long long c = N - n0 < C ? N - n0 : C;
+            cudaError_t e = h->ops->fields_nodes(k, h->pop[0], st, st + c, st + (1 + h->D) * c, n0, c,
+                                                 status_ptr(h), h->stream, &h->launches);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(rho + n0, st, c * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            for (int d = 0; d < h->D && e == cudaSuccess; ++d)
+                e = cudaMemcpyAsync(u + d * N + n0, st + (1 + d) * c, c * sizeof(double), cudaMemcpyDeviceToHost,
+                                    h->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(T + n0, st + (1 + h->D) * c, c * sizeof(double), cudaMemcpyDeviceToHost,
+                                    h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // the staging area is reused
+            if (e != cudaSuccess) return ELBM_ERR_CUDA;
+        }
+        return sync_status(h);
+    }
     const size_t N = (size_t)h->N;
     double* st = staging(h);
     int rc = elbm_get_fields_device(h, st, st + N, st + (1 + h->D) * N);
@@ -282,7 +379,8 @@ int elbm_get_fields(elbm_handle* h, double* rho, double* u, double* T) {
 int elbm_conservation(elbm_handle* h, double out[5]) {
     if (!h || !h->bound || !out) return ELBM_ERR_ARG;
     int nb = 0;
-    cudaError_t e = h->ops->conservation(h->kp, h->pop[h->cur], query_partials(h), &nb, h->stream, &h->launches);
+    cudaError_t e = h->ops->conservation(diag_params(h), h->pop[h->cur], query_partials(h), &nb, h->stream,
+                                         &h->launches);
     if (e != cudaSuccess) return ELBM_ERR_CUDA;
     return finalize_to_host(h, query_partials(h), nb, out);
 }
@@ -291,7 +389,7 @@ int elbm_turbulence_stats(elbm_handle* h, double out[13]) {
     if (!h || !h->bound || !out) return ELBM_ERR_ARG;
     int nb = 0;
     double* part = query_partials(h);   // kStatsSums values x (<= max_blocks) CTAs
-    cudaError_t e = h->ops->stats(h->kp, h->pop[h->cur], part, &nb, h->stream, &h->launches);
+    cudaError_t e = h->ops->stats(diag_params(h), h->pop[h->cur], part, &nb, h->stream, &h->launches);
     if (e != cudaSuccess) return ELBM_ERR_CUDA;
     double sums[kStatsSums];
     const int rc = finalize_to_host(h, part, nb, sums, kStatsSums);
@@ -327,7 +425,17 @@ int elbm_set_kernel(elbm_handle* h, int kernel) {
                kernel != ELBM_KERNEL_FUSED_TMA))
         return ELBM_ERR_ARG;
     if (kernel == ELBM_KERNEL_FUSED_TMA && !h->ops->tma_supported(h->kp)) return ELBM_ERR_UNSUPPORTED;
+    if (h->layout == ELBM_LAYOUT_AA && kernel != ELBM_KERNEL_TWOPASS) return ELBM_ERR_UNSUPPORTED;
     h->kernel = kernel;
+    return ELBM_OK;
+}
+
+int elbm_set_layout(elbm_handle* h, int layout) {
+    if (!h || h->bound || (layout != ELBM_LAYOUT_PINGPONG && layout != ELBM_LAYOUT_AA)) return ELBM_ERR_ARG;
+    if (layout == ELBM_LAYOUT_AA && !(h->kp.per_x && h->kp.per_y && h->kp.per_z)) return ELBM_ERR_UNSUPPORTED;
+    h->layout = layout;
+    h->kernel = layout == ELBM_LAYOUT_AA ? ELBM_KERNEL_TWOPASS : ELBM_KERNEL_FUSED;
+    compute_aux(h);
     return ELBM_OK;
 }
 

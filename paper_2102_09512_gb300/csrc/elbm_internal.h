@@ -276,6 +276,17 @@ struct Ops {
     // the default fused step given src's tensor map (L2 prefetch of the planes ahead)
     cudaError_t (*step_fused_pf)(const KParams& p, const void* src, void* dst, const CUtensorMap* src_map,
                                  double* partials, int* nblocks, int* status, cudaStream_t s, long long* launches);
+    // equilibria of nodes n0 .. n0 + cnt - 1 written in place (fields of those nodes only),
+    // and rho, u, T of such a range (chunked host transfers)
+    cudaError_t (*init_nodes)(const KParams& p, const double* rho, const double* u, const double* T, void* pop,
+                              long long n0, long long cnt, int* status, cudaStream_t s, long long* launches);
+    cudaError_t (*fields_nodes)(const KParams& p, const void* pop, double* rho, double* u, double* T,
+                                long long n0, long long cnt, int* status, cudaStream_t s, long long* launches);
+    // AA single-store layout (periodic grids): one two-pass step on the store A from layout
+    // L1 (from_l1 = 1: node-local reads, swapped writes) or from layout L0 (pulled reads,
+    // pushed writes)
+    cudaError_t (*step_aa)(const KParams& p, void* A, void* qfield, double* partials, int* nblocks, int* status,
+                           cudaStream_t s, long long* launches, int from_l1);
 };
 
 // z-segment length of the fused D3Q27 kernels.  Each CTA marches one (tile, segment)

@@ -138,11 +138,27 @@ __device__ __forceinline__ void gather(const KParams& p, const P* __restrict__ s
     }
 }
 
+// The post-collision pairs C(X_n)_i of node n as stored: in place (p.aa = 0), or in the AA
+// single-store layouts (p.aa = 1: direction i at opp(i) of the node; p.aa = 2: direction i
+// pushed to the node's neighbour n + c_i, periodic).
 __device__ __forceinline__ void load_local(const KParams& p, const P* __restrict__ pop, long long n, R* f,
                                            R* g) {
+    if (p.aa == 0) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-        Cd::dec(pop[(size_t)i * (size_t)p.N + (size_t)n], f[i], g[i]);
+        for (int i = 0; i < Q; ++i) Cd::dec(pop[(size_t)i * (size_t)p.N + (size_t)n], f[i], g[i]);
+    } else if (p.aa == 1) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Cd::dec(pop[(size_t)(Q - 1 - i) * (size_t)p.N + (size_t)n], f[i], g[i]);
+    } else {
+        const int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((long long)p.nx * p.ny));
+        PullRows r;
+        pull_rows(p, x, y, z, r);   // the pull source of opp(i) is n + c_i
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int k = Q - 1 - i, a = k % 3, b = (k / 3) % 3, c = (kD == 3) ? k / 9 : 1;
+            Cd::dec(*((pop + (size_t)i * (size_t)p.N) + (unsigned)(r.row[b][c] + r.xs[a])), f[i], g[i]);
+        }
+    }
 }
 
 __device__ __forceinline__ void store_node(const KParams& p, P* __restrict__ dst, long long n, const R* f,
@@ -269,14 +285,17 @@ __device__ __forceinline__ void cp_async_wait_pending() {
 // ---------------------------------------------------------------------------
 // initial state and field extraction
 // ---------------------------------------------------------------------------
+// Nodes n0 .. n0 + cnt - 1; the fields hold those nodes only (u component-major with
+// stride cnt).
 __global__ void init_kernel(const __grid_constant__ KParams p, const double* __restrict__ rho,
                             const double* __restrict__ u, const double* __restrict__ T,
-                            P* __restrict__ pop, int* __restrict__ status) {
-    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+                            P* __restrict__ pop, int* __restrict__ status, long long n0, long long cnt) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = n0 + k;
     bool bad = false;
-    if (n < p.N) {
-        const R r = (R)rho[n], t = (R)T[n];
-        const R ux = (R)u[n], uy = (R)u[p.N + n], uz = kD == 3 ? (R)u[2 * p.N + n] : R(0);
+    if (k < cnt) {
+        const R r = (R)rho[k], t = (R)T[k];
+        const R ux = (R)u[k], uy = (R)u[cnt + k], uz = kD == 3 ? (R)u[2 * cnt + k] : R(0);
         bad = !(r > R(0)) || !(t > R(0)) || !isfinite(r) || !isfinite(t) || !isfinite(ux) ||
               !isfinite(uy) || !isfinite(uz);
         R f[Q], g[Q];
@@ -293,21 +312,23 @@ __global__ void init_kernel(const __grid_constant__ KParams p, const double* __r
     flag_if(bad, status);
 }
 
+// Nodes n0 .. n0 + cnt - 1 into fields of cnt nodes (u component-major with stride cnt).
 __global__ void fields_kernel(const __grid_constant__ KParams p, const P* __restrict__ pop,
                               double* __restrict__ rho, double* __restrict__ u,
-                              double* __restrict__ T, int* __restrict__ status) {
-    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+                              double* __restrict__ T, int* __restrict__ status, long long n0, long long cnt) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = n0 + k;
     bool bad = false;
-    if (n < p.N) {
+    if (k < cnt) {
         R f[Q], g[Q];
         load_local(p, pop, n, f, g);
         Moments<R> m;
         node_moments<kD, R, false, DEV>(f, g, p, m);
-        rho[n] = m.rho;
-        u[n] = m.ux;
-        u[p.N + n] = m.uy;
-        if (kD == 3) u[2 * p.N + n] = m.uz;
-        T[n] = m.T;
+        rho[k] = m.rho;
+        u[k] = m.ux;
+        u[cnt + k] = m.uy;
+        if (kD == 3) u[2 * cnt + k] = m.uz;
+        T[k] = m.T;
         bad = nonphysical(m);
     }
     flag_if(bad, status);
@@ -350,10 +371,11 @@ __global__ void totals_kernel(const __grid_constant__ KParams p, const P* __rest
 // Velocity of node n from its f values only (rho and rho u).
 __device__ __forceinline__ void node_velocity(const KParams& p, const P* __restrict__ pop, long long n, R u[3]) {
     R rho = 0, j[3] = {0, 0, 0};
+    R fs[Q], gs[Q];
+    load_local(p, pop, n, fs, gs);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        R f, g;
-        Cd::dec(pop[(size_t)i * (size_t)p.N + (size_t)n], f, g);
+        const R f = fs[i];
         rho += f;
         if (cx_of(i)) j[0] += cx_of(i) * f;
         if (cy_of(i)) j[1] += cy_of(i) * f;
@@ -495,6 +517,102 @@ __global__ void collide_kernel(const __grid_constant__ KParams p, const P* __res
         node_totals(m, m.rE, tot);
         collide<kD, R, DEV>(f, g, m, Dx, Dy, Dz, p);
         store_node(p, dst, n, f, g);
+    }
+    flag_if(bad, status);
+    block_sum5_warp(tot, partials + 5 * blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// AA single-store layout (periodic grids, two-pass schedule)
+// ---------------------------------------------------------------------------
+// One store A holds the post-collision state C(X_n) in one of two layouts that alternate
+// with the step:
+//   L0: C(X_n)_i(x) at A[opp(i)][x]          (swapped at the node)
+//   L1: C(X_n)_i(x) at A[i][x + c_i]         (pushed to the neighbour, periodic wrap)
+// A step from L0 pulls f_i(y) = C(X_n)_i(y - c_i) = A[opp(i)][y - c_i] and pushes the new
+// C(X_n+1)_i(y) to A[i][y + c_i] (-> L1); a step from L1 reads f_i(y) = A[i][y] at the node
+// itself and writes C(X_n+1)_i(y) to A[opp(i)][y] (-> L0).  In both, the slots a node
+// writes are exactly the slots it read (for a step from L0, direction i's write target
+// A[i][y + c_i] is direction opp(i)'s source), so with the Q~ field computed in a first pass
+// every slot is read and written by one thread only.  A periodic map is a bijection; a
+// clamped (zero-gradient) face would let two nodes read one slot that one of them writes.
+__host__ __device__ constexpr int opp(int i) { return Q - 1 - i; }
+
+// Address of direction j's pair in the row/column of direction k's pull source (PullRows of
+// the node): a step from L0 reads A[opp(i)] at the source of i and writes A[i] at the
+// source of opp(i).
+__device__ __forceinline__ P* aa_ptr(const KParams& p, P* A, const PullRows& r, int j, int k) {
+    const int a = k % 3, b = (k / 3) % 3, c = (kD == 3) ? k / 9 : 1;
+    return (A + (size_t)j * (size_t)p.N) + (unsigned)(r.row[b][c] + r.xs[a]);
+}
+
+template <bool FROM_L1>
+__device__ __forceinline__ void aa_gather(const KParams& p, P* A, const PullRows& r, long long n, R* f, R* g) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const P v = FROM_L1 ? A[(size_t)i * (size_t)p.N + (size_t)n] : *aa_ptr(p, A, r, opp(i), i);
+        Cd::dec(v, f[i], g[i]);
+    }
+}
+template <bool FROM_L1>
+__device__ __forceinline__ void aa_store(const KParams& p, P* A, const PullRows& r, long long n, const R* f,
+                                         const R* g) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const P v = Cd::enc(f[i], g[i]);
+        if (FROM_L1) A[(size_t)opp(i) * (size_t)p.N + (size_t)n] = v;
+        else *aa_ptr(p, A, r, i, opp(i)) = v;
+    }
+}
+
+// Pass 1 of an AA step: Q~_aaa of every node from its post-stream populations.
+template <bool FROM_L1>
+__global__ void aa_moments_kernel(const __grid_constant__ KParams p, P* A, R* __restrict__ qf) {
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    const int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((long long)p.nx * p.ny));
+    PullRows r;
+    if (!FROM_L1) pull_rows(p, x, y, z, r);
+    R f[Q], g[Q];
+    aa_gather<FROM_L1>(p, A, r, n, f, g);
+    Moments<R> m;
+    node_moments<kD, R, false, DEV>(f, g, p, m);
+    qf[n] = anomaly(m.rho, m.ux, m.T);
+    qf[p.N + n] = anomaly(m.rho, m.uy, m.T);
+    if (kD == 3) qf[2 * p.N + n] = anomaly(m.rho, m.uz, m.T);
+}
+
+// Pass 2 of an AA step: the same reads, the derivative of Q~ from the field, collision, and
+// the writes into the slots just read.
+template <bool FROM_L1>
+__global__ void aa_collide_kernel(const __grid_constant__ KParams p, P* A, const R* __restrict__ qf,
+                                  double* __restrict__ partials, int* __restrict__ status) {
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    R tot[5] = {0, 0, 0, 0, 0};
+    bool bad = false;
+    if (n < p.N) {
+        const int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((long long)p.nx * p.ny));
+        PullRows r;
+        if (!FROM_L1) pull_rows(p, x, y, z, r);
+        R f[Q], g[Q];
+        aa_gather<FROM_L1>(p, A, r, n, f, g);
+        Moments<R> m;
+        node_moments<kD, R, true, DEV>(f, g, p, m);
+        bad = nonphysical(m);
+        const long long N = p.N;
+        const int xm = map_axis(x - 1, p.nx, p.per_x), xp = map_axis(x + 1, p.nx, p.per_x);
+        const int ym = map_axis(y - 1, p.ny, p.per_y), yp = map_axis(y + 1, p.ny, p.per_y);
+        const R Dx = dQ(p.deriv, m.ux, qf[node_index(p, xm, y, z)], qf[n], qf[node_index(p, xp, y, z)]);
+        const R Dy = dQ(p.deriv, m.uy, qf[N + node_index(p, x, ym, z)], qf[N + n], qf[N + node_index(p, x, yp, z)]);
+        R Dz = R(0);
+        if (kD == 3) {
+            const int zm = map_axis(z - 1, p.nz, p.per_z), zp = map_axis(z + 1, p.nz, p.per_z);
+            Dz = dQ(p.deriv, m.uz, qf[2 * N + node_index(p, x, y, zm)], qf[2 * N + n],
+                    qf[2 * N + node_index(p, x, y, zp)]);
+        }
+        node_totals(m, m.rE, tot);
+        collide<kD, R, DEV>(f, g, m, Dx, Dy, Dz, p);
+        aa_store<FROM_L1>(p, A, r, n, f, g);
     }
     flag_if(bad, status);
     block_sum5_warp(tot, partials + 5 * blockIdx.x);
@@ -1702,16 +1820,52 @@ cudaError_t launch_init(const KParams& p, const double* rho, const double* u, co
     // Moments of C(X_n) equal those of X_n (the collision conserves them), so field
     // extraction and totals read each node's own values.
     const unsigned nb = blocks_1d(p.N);
-    init_kernel<<<nb, kThreads, 0, s>>>(p, rho, u, T, (P*)spare, status);
+    init_kernel<<<nb, kThreads, 0, s>>>(p, rho, u, T, (P*)spare, status, 0, p.N);
     moments_kernel<false><<<nb, kThreads, 0, s>>>(p, (const P*)spare, (R*)qfield);
     collide_kernel<false><<<nb, kThreads, 0, s>>>(p, (const P*)spare, (P*)pop, (const R*)qfield, partials, status);
     *launches += 3;
     return cudaGetLastError();
 }
 
+// f^eq, g^eq of nodes n0 .. n0 + cnt - 1 written in place into pop (fields of those nodes
+// only).  For the AA single store this is the first half of initialisation: a step from
+// layout L1 (node-local reads, swapped writes) then collides the equilibria without
+// streaming, leaving C(X_0) in layout L0.
+cudaError_t launch_init_nodes(const KParams& p, const double* rho, const double* u, const double* T, void* pop,
+                              long long n0, long long cnt, int* status, cudaStream_t s, long long* launches) {
+    init_kernel<<<blocks_1d(cnt), kThreads, 0, s>>>(p, rho, u, T, (P*)pop, status, n0, cnt);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+// rho, u, T of nodes n0 .. n0 + cnt - 1 into fields of cnt nodes.
+cudaError_t launch_fields_nodes(const KParams& p, const void* pop, double* rho, double* u, double* T,
+                                long long n0, long long cnt, int* status, cudaStream_t s, long long* launches) {
+    fields_kernel<<<blocks_1d(cnt), kThreads, 0, s>>>(p, (const P*)pop, rho, u, T, status, n0, cnt);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+// One AA step on the single store A: from layout L1 (node-local reads, swapped writes) or
+// from L0 (pulled reads, pushed writes).
+cudaError_t launch_step_aa(const KParams& p, void* A, void* qfield, double* partials, int* nblocks, int* status,
+                           cudaStream_t s, long long* launches, int from_l1) {
+    const unsigned nb = blocks_1d(p.N);
+    if (from_l1) {
+        aa_moments_kernel<true><<<nb, kThreads, 0, s>>>(p, (P*)A, (R*)qfield);
+        aa_collide_kernel<true><<<nb, kThreads, 0, s>>>(p, (P*)A, (const R*)qfield, partials, status);
+    } else {
+        aa_moments_kernel<false><<<nb, kThreads, 0, s>>>(p, (P*)A, (R*)qfield);
+        aa_collide_kernel<false><<<nb, kThreads, 0, s>>>(p, (P*)A, (const R*)qfield, partials, status);
+    }
+    *launches += 2;
+    *nblocks = (int)nb;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fields(const KParams& p, const void* pop, double* rho, double* u, double* T, int* status,
                           cudaStream_t s, long long* launches) {
-    fields_kernel<<<blocks_1d(p.N), kThreads, 0, s>>>(p, (const P*)pop, rho, u, T, status);
+    fields_kernel<<<blocks_1d(p.N), kThreads, 0, s>>>(p, (const P*)pop, rho, u, T, status, 0, p.N);
     ++*launches;
     return cudaGetLastError();
 }
@@ -1941,7 +2095,7 @@ const Ops kOps = {kD,          kST,           sizeof(P) / 2,  sizeof(R),        
                   launch_init, launch_fields, launch_twopass, launch_fused_default, launch_fused_reread,
                   launch_totals, launch_ensemble, ensemble_occupancy, launch_stats,
                   kD == 3 ? (kPipe ? kTYP : kTY3) : 1, fused_occupancy, launch_fused_tma, tma_supported, encode_tmap,
-                  launch_fused_pf};
+                  launch_fused_pf, launch_init_nodes, launch_fields_nodes, launch_step_aa};
 
 }  // namespace
 

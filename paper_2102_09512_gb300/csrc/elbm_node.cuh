@@ -33,6 +33,8 @@ struct KParams {
     int tz;                      // segment length of the fused kernels (D3Q27: z planes, D2Q9: rows)
     int tile2d;                  // D2Q9: the default fused schedule runs the one-tile-per-CTA kernel
                                  // (grids whose row march would not fill the device)
+    int aa;                      // layout of the store read by the diagnostics: 0 in place; AA single
+                                 // store: 1 swapped at the node, 2 pushed to the neighbour
     float2 rest2[27];            // rest-state pair (f_i, g_i) of every direction, deviation stores
     float rest_rho, rest_Pxx, rest_Pyy, rest_Pzz, rest_E;   // their moment sums
     // The same parameters precomputed in both arithmetic types, so that no kernel

@@ -26,6 +26,7 @@ ELBM_F64, ELBM_F32, ELBM_F16DEV, ELBM_BF16DEV = 0, 1, 2, 3
 ELBM_DERIV_UPWIND, ELBM_DERIV_CENTRAL = 0, 1
 ELBM_KERNEL_FUSED, ELBM_KERNEL_TWOPASS, ELBM_KERNEL_FUSED_REREAD, ELBM_KERNEL_FUSED_TMA = 0, 1, 2, 3
 ELBM_ENSEMBLE_PERSISTENT, ELBM_ENSEMBLE_PER_INSTANCE = 0, 1
+ELBM_LAYOUT_PINGPONG, ELBM_LAYOUT_AA = 0, 1
 
 STORES = {"f64": ELBM_F64, "f32": ELBM_F32, "f16dev": ELBM_F16DEV, "bf16dev": ELBM_BF16DEV}
 VALUE_BYTES = {ELBM_F64: 8, ELBM_F32: 4, ELBM_F16DEV: 2, ELBM_BF16DEV: 2}
@@ -70,6 +71,7 @@ _SIGS = {
     "elbm_step_totals": (ctypes.c_int, [_vp, _dp]),
     "elbm_turbulence_stats": (ctypes.c_int, [_vp, _dp]),
     "elbm_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "elbm_set_layout": (ctypes.c_int, [_vp, ctypes.c_int]),
     "elbm_inject_wait_timeout": (ctypes.c_int, [_vp, ctypes.c_int]),
     "elbm_set_tile_z": (ctypes.c_int, [_vp, ctypes.c_int]),
     "elbm_get_populations": (ctypes.c_int, [_vp, _vp]),
@@ -195,6 +197,10 @@ def elbm_turbulence_stats(h) -> dict:
 
 def elbm_set_kernel(h, kernel: int):
     _check(lib().elbm_set_kernel(h, int(kernel)), "elbm_set_kernel")
+
+
+def elbm_set_layout(h, layout: int):
+    _check(lib().elbm_set_layout(h, int(layout)), "elbm_set_layout")
 
 
 def elbm_inject_wait_timeout(h, on: int):
@@ -335,23 +341,28 @@ def make_params(lattice, nx, ny, nz=1, gamma=1.4, Pr=0.71, mu0=1e-3, T0=0.15, mu
 class Solver:
     """One lattice with caller-owned (torch) device buffers bound to a stream."""
 
-    def __init__(self, params: elbm_params, device="cuda", stream=None):
+    def __init__(self, params: elbm_params, device="cuda", stream=None, layout=ELBM_LAYOUT_PINGPONG):
         import torch
 
         self.torch = torch
         self.params = params
+        self.layout = layout
         self.D = 3 if params.lattice == ELBM_D3Q27 else 2
         self.N = params.nx * params.ny * params.nz
         self.h = elbm_create(params)
         try:
+            if layout != ELBM_LAYOUT_PINGPONG:
+                elbm_set_layout(self.h, layout)
             self.pop_bytes, self.aux_bytes = elbm_bytes_required(self.h)
             dev = torch.device(device)
             self.pop_a = torch.empty(self.pop_bytes, dtype=torch.uint8, device=dev)
-            self.pop_b = torch.empty(self.pop_bytes, dtype=torch.uint8, device=dev)
+            # the AA layout updates one store in place
+            self.pop_b = None if layout == ELBM_LAYOUT_AA else torch.empty(self.pop_bytes, dtype=torch.uint8,
+                                                                             device=dev)
             self.aux = torch.empty(self.aux_bytes, dtype=torch.uint8, device=dev)
             self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
-            elbm_bind(self.h, self.pop_a.data_ptr(), self.pop_b.data_ptr(), self.aux.data_ptr(),
-                      self.stream.cuda_stream)
+            elbm_bind(self.h, self.pop_a.data_ptr(), 0 if self.pop_b is None else self.pop_b.data_ptr(),
+                      self.aux.data_ptr(), self.stream.cuda_stream)
         except Exception:
             elbm_destroy(self.h)
             self.h = None

@@ -156,3 +156,34 @@ def test_grid_size_limit(L):
     with pytest.raises(L.ElbmError) as ei:
         L.elbm_create(L.make_params(3, 2048, 1024, 1025, store="f16dev"))
     assert ei.value.code == L.ELBM_ERR_UNSUPPORTED
+
+
+def test_aa_layout_host_checks(L):
+    """The single-store (AA) layout: periodic grids only, selected before binding, the
+    two-pass schedule only, and a staging area of at most 2^25 nodes for host transfers."""
+    p = L.make_params(3, 64, 48, 40, store="f32")
+    h = L.elbm_create(p)
+    L.elbm_set_layout(h, L.ELBM_LAYOUT_AA)
+    pop, aux = L.elbm_bytes_required(h)
+    assert pop == 2 * 27 * 64 * 48 * 40 * 4   # the size of one store
+    assert L.lib().elbm_set_kernel(h, L.ELBM_KERNEL_FUSED) == L.ELBM_ERR_UNSUPPORTED
+    assert L.lib().elbm_set_kernel(h, L.ELBM_KERNEL_FUSED_REREAD) == L.ELBM_ERR_UNSUPPORTED
+    assert L.lib().elbm_set_kernel(h, L.ELBM_KERNEL_TWOPASS) == L.ELBM_OK
+    assert L.lib().elbm_set_layout(h, 7) == L.ELBM_ERR_ARG
+    L.elbm_destroy(h)
+    # a zero-gradient axis: two nodes would read a slot that one of them writes
+    for bc in [(1, 1, 0, 0, 0, 0), (0, 0, 0, 0, 1, 1)]:
+        h = L.elbm_create(L.make_params(3, 16, 16, 16, bc=bc, store="f64"))
+        assert L.lib().elbm_set_layout(h, L.ELBM_LAYOUT_AA) == L.ELBM_ERR_UNSUPPORTED
+        L.elbm_destroy(h)
+    # 1024^3 FP32: one store of 232 GB and a small auxiliary buffer (Q~ field and a
+    # chunk-sized staging area) fit a GB300, where ping-pong stores would not
+    h = L.elbm_create(L.make_params(3, 1024, 1024, 1024, store="f32"))
+    pp_pop, pp_aux = L.elbm_bytes_required(h)
+    L.elbm_set_layout(h, L.ELBM_LAYOUT_AA)
+    pop, aux = L.elbm_bytes_required(h)
+    n = 1024 ** 3
+    assert pop == pp_pop == 27 * n * 8
+    assert aux < 3 * n * 4 + (5 * 8 << 25) + (1 << 30)
+    assert pop + aux < 260e9 < 2 * pp_pop
+    L.elbm_destroy(h)

@@ -1,0 +1,194 @@
+"""GPU tests of the single-store (AA) layout: one population store updated in place, its
+layout alternating with the step parity, on the two-pass schedule, for periodic grids.
+
+The AA kernels run the same per-node arithmetic as the ping-pong two-pass kernels
+(moments, Q~ field, collision) and differ only in where each pair is read and written.
+With the FP32-arithmetic stores (FP32, FP16 and BF16 deviations) the fields, totals and
+statistics after any number of steps are bit for bit those of the two-pass ping-pong
+schedule; with the FP64 store the compiler contracts a few multiply-adds of the two
+kernels differently, and they agree to the last bits (1e-14 relative).  Against the FP64
+oracle they meet the parity bounds.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2102_09512_gb300 import cases as C
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16dev": 1e-3}
+U0 = (0.09, -0.07, 0.06)
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2102_09512_gb300 import build as B
+    B.build()
+    O.build()
+    from paper_2102_09512_gb300 import elbm
+    return elbm
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+CASES = {
+    2: lambda: C.random_smooth(2, 45, 29, 1, seed=141, mu0=0.01, du=0.05, u0=U0),
+    3: lambda: C.random_smooth(3, 37, 21, 19, seed=142, mu0=0.01, du=0.05, u0=U0),
+}
+
+
+def pair(E, c, store):
+    aa = E.Solver.from_case(c, store=store, layout=E.ELBM_LAYOUT_AA)
+    pp = E.Solver.from_case(c, store=store)
+    pp.set_kernel(E.ELBM_KERNEL_TWOPASS)
+    return aa, pp
+
+
+@pytest.mark.parametrize("store", ["f64", "f32", "f16dev", "bf16dev"])
+@pytest.mark.parametrize("D", [2, 3])
+def test_aa_equals_pingpong_twopass(E, D, store):
+    """After 0, 1, 2, 7 and 20 steps (both layouts, in either order) the fields, the FP64
+    totals, the step totals and the turbulence statistics equal the ping-pong two-pass
+    schedule's (bit for bit; FP64 to 1e-14)."""
+    c = CASES[D]()
+    aa, pp = pair(E, c, store)
+
+    def same(a, b):
+        if store == "f64":
+            return rel_l2(a, b) <= 1e-14
+        return np.array_equal(a, b)
+
+    done = 0
+    for k in (0, 1, 2, 7, 20):
+        aa.step(k - done)
+        pp.step(k - done)
+        done = k
+        for x, y in zip(aa.fields(), pp.fields()):
+            assert same(x, y), (k, store)
+        assert same(aa.conservation(), pp.conservation()), k
+        if k > 0:
+            assert same(aa.step_totals(), pp.step_totals()), k
+        sa, sp = aa.turbulence_stats(), pp.turbulence_stats()
+        assert same(np.array(list(sa.values())), np.array(list(sp.values()))), k
+    aa.close()
+    pp.close()
+
+
+@pytest.mark.parametrize("steps", [29, 30])
+@pytest.mark.parametrize("store", ["f64", "f32", "f16dev"])
+@pytest.mark.parametrize("D", [2, 3])
+def test_aa_matches_oracle(E, D, store, steps):
+    c = CASES[D]()
+    p = O.Params(D=c.D, nx=c.nx, ny=c.ny, nz=c.nz, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0,
+                 mu_exp=c.mu_exp, bc=c.bc)
+    s = O.init(p, c.rho, c.u, c.T)
+    O.step(s, steps)
+    ref = O.fields(s)
+    g = E.Solver.from_case(c, store=store, layout=E.ELBM_LAYOUT_AA)
+    g.step(steps)
+    for a, b in zip(g.fields(), ref):
+        assert rel_l2(a, b) <= TOL[store], (D, store, steps)
+    g.close()
+
+
+def test_aa_checkpoint_restart(E):
+    """A raw copy of the single store, restored into a handle at the same step parity,
+    continues exactly."""
+    c = CASES[3]()
+    for first in (4, 5):
+        a = E.Solver.from_case(c, store="f32", layout=E.ELBM_LAYOUT_AA)
+        a.step(first)
+        snap = a.get_populations()
+        a.step(6)
+        ref = a.fields()
+        b = E.Solver.from_case(c, store="f32", layout=E.ELBM_LAYOUT_AA)
+        b.step(first % 2)   # the same parity as the snapshot
+        b.set_populations(snap)
+        b.step(6)
+        for x, y in zip(b.fields(), ref):
+            assert np.array_equal(x, y), first
+        a.close()
+        b.close()
+
+
+def test_aa_power_law_caloric_and_central(E):
+    """The options of the collision (power-law viscosity, cubic Cv(T), central derivative)
+    on the AA layout give the ping-pong two-pass results (FP32 bit for bit)."""
+    c = C.random_smooth(3, 24, 17, 10, seed=143, mu0=0.01, mu_exp=0.76, dT=0.04, du=0.05, u0=U0)
+    c.cv = (1.0, 4.0, -4.0, 5.0)
+    for store in ("f64", "f32"):
+        aa = E.Solver.from_case(c, store=store, layout=E.ELBM_LAYOUT_AA, deriv=E.ELBM_DERIV_CENTRAL)
+        pp = E.Solver.from_case(c, store=store, deriv=E.ELBM_DERIV_CENTRAL)
+        pp.set_kernel(E.ELBM_KERNEL_TWOPASS)
+        aa.step(9)
+        pp.step(9)
+        for x, y in zip(aa.fields(), pp.fields()):
+            assert (rel_l2(x, y) <= 1e-14) if store == "f64" else np.array_equal(x, y), store
+        aa.close()
+        pp.close()
+
+
+def test_aa_chunked_host_transfers(E):
+    """A grid above the 2^25-node staging chunk (8192 x 4200 D2Q9, 34.4 M nodes): the
+    fields go in and out in two chunks and equal the ping-pong two-pass run's."""
+    import torch
+    c = C.random_smooth(2, 8192, 4200, 1, seed=144, mu0=0.01, du=0.05, u0=U0)
+    aa, pp = pair(E, c, "f32")
+    aa.step(3)
+    pp.step(3)
+    for x, y in zip(aa.fields(), pp.fields()):
+        assert np.array_equal(x, y)
+    aa.close()
+    pp.close()
+    torch.cuda.empty_cache()
+
+
+def test_aa_1024cube_fp32_on_one_gpu(E):
+    """The grid the single store is for: D3Q27 at 1024^3 (1.07 G nodes) with FP32 pairs,
+    232 GB of populations that ping-pong stores would need twice.  A smooth field with a
+    mean flow, one step: sampled nodes (corners of the box and random ones) equal the
+    oracle's values computed on their 5^3 neighbourhoods, and the totals are conserved
+    over two more steps (both layouts)."""
+    import torch
+    n = 1024
+    ax = 2.0 * np.pi * np.arange(n) / n
+    cx, cy, cz = np.cos(ax)[None, None, :], np.cos(2 * ax)[None, :, None], np.cos(3 * ax)[:, None, None]
+    c = C.Case("smooth_1024", 3, n, n, n, None, None, None, mu0=0.01, T0=0.15)
+    c.rho = 1.0 + 0.02 * cx * cy * cz
+    c.T = np.empty((n, n, n))
+    c.T[...] = 0.15 + 0.01 * cy * cz
+    c.u = np.empty((3, n, n, n))
+    c.u[0] = U0[0] + 0.03 * cz * cy
+    c.u[1] = U0[1] + 0.03 * cx * cz
+    c.u[2] = U0[2] + 0.03 * cx * cy
+    g = E.Solver.from_case(c, store="f32", layout=E.ELBM_LAYOUT_AA)
+    assert g.pop_b is None and g.pop_bytes == 27 * n ** 3 * 8
+    t0 = g.conservation()
+    g.step(1)
+    rho, u, T = g.fields()
+    rng = np.random.default_rng(12)
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1)] + [tuple(v) for v in rng.integers(0, n, size=(6, 3))]
+    for x, y, z in pts:
+        k = x + n * (y + n * z)
+        idx = [(np.arange(-2, 3) + v) % n for v in (x, y, z)]
+        sub = np.ix_(idx[2], idx[1], idx[0])
+        p = O.Params(D=3, nx=5, ny=5, nz=5, gamma=c.gamma, Pr=c.Pr, mu0=c.mu0, T0=c.T0, mu_exp=c.mu_exp,
+                     bc=(1, 1, 1, 1, 1, 1))
+        s = O.init(p, c.rho[sub], np.stack([c.u[a][sub] for a in range(3)]), c.T[sub])
+        O.step(s, 1)
+        r_o, u_o, T_o = O.fields(s)
+        assert abs(rho[k] - r_o[62]) <= 2e-6 * abs(r_o[62])
+        assert abs(T[k] - T_o[62]) <= 2e-6 * abs(T_o[62])
+        assert np.max(np.abs(u[:, k] - u_o[:, 62])) <= 1e-6
+    del rho, u, T
+    g.step(2)
+    t1 = g.conservation()
+    assert abs(t1[0] - t0[0]) / t0[0] < 1e-6 and abs(t1[4] - t0[4]) / t0[4] < 1e-6
+    g.close()
+    del g
+    torch.cuda.empty_cache()
