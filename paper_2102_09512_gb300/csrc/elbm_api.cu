@@ -23,6 +23,7 @@ struct elbm_handle {
     AuxLayout aux;
     void* pop[2];
     CUtensorMap tmap[2];     // tensor maps of pop[0], pop[1] (TMA-staged D3Q27 kernel)
+    CUtensorMap pfmap[2];    // ... with the L2-prefetch boxes of the default fused kernel
     bool tmap_ready;
     char* auxp;
     cudaStream_t stream;
@@ -227,8 +228,10 @@ int elbm_bind(elbm_handle* h, void* pop_a, void* pop_b, void* aux, void* stream)
     h->pop[1] = pop_b;
     h->tmap_ready = false;
     if (!aa && h->ops->tma_supported(h->kp))
-        h->tmap_ready = h->ops->encode_tmap(h->kp, pop_a, &h->tmap[0]) == 1 &&
-                        h->ops->encode_tmap(h->kp, pop_b, &h->tmap[1]) == 1;
+        h->tmap_ready = h->ops->encode_tmap(h->kp, pop_a, &h->tmap[0], kTmapStage) == 1 &&
+                        h->ops->encode_tmap(h->kp, pop_b, &h->tmap[1], kTmapStage) == 1 &&
+                        h->ops->encode_tmap(h->kp, pop_a, &h->pfmap[0], kTmapPrefetch) == 1 &&
+                        h->ops->encode_tmap(h->kp, pop_b, &h->pfmap[1], kTmapPrefetch) == 1;
     h->auxp = (char*)aux;
     h->stream = (cudaStream_t)stream;
     h->cur = 0;
@@ -322,7 +325,7 @@ int elbm_step(elbm_handle* h, int nsteps) {
                                        status_ptr(h), h->stream, &h->launches);
         }
         else if (h->tmap_ready)
-            e = h->ops->step_fused_pf(h->kp, src, dst, &h->tmap[h->cur], step_partials(h), &h->step_blocks,
+            e = h->ops->step_fused_pf(h->kp, src, dst, &h->pfmap[h->cur], step_partials(h), &h->step_blocks,
                                       status_ptr(h), h->stream, &h->launches);
         else
             e = h->ops->step_fused(h->kp, src, dst, step_partials(h), &h->step_blocks, status_ptr(h), h->stream,

@@ -271,9 +271,11 @@ struct Ops {
     cudaError_t (*step_fused_tma)(const KParams& p, const void* src, void* dst, const CUtensorMap* src_map,
                                   double* partials, int* nblocks, int* status, cudaStream_t s, long long* launches);
     int (*tma_supported)(const KParams& p);   // the grid suits the TMA-staged D3Q27 kernel
-    // tensor map of a store for that kernel: 1 made, 0 not applicable, -1 the driver refused
-    int (*encode_tmap)(const KParams& p, const void* base, CUtensorMap* out);
-    // the default fused step given src's tensor map (L2 prefetch of the planes ahead)
+    // tensor map of a store: 1 made, 0 not applicable, -1 the driver refused.  kind
+    // kTmapStage: the boxes the TMA-staged kernel copies; kTmapPrefetch: the boxes the
+    // default fused kernel prefetches into L2
+    int (*encode_tmap)(const KParams& p, const void* base, CUtensorMap* out, int kind);
+    // the default fused step given src's prefetch tensor map (L2 prefetch of the planes ahead)
     cudaError_t (*step_fused_pf)(const KParams& p, const void* src, void* dst, const CUtensorMap* src_map,
                                  double* partials, int* nblocks, int* status, cudaStream_t s, long long* launches);
     // equilibria of nodes n0 .. n0 + cnt - 1 written in place (fields of those nodes only),
@@ -332,6 +334,8 @@ inline void plan_d2q9(KParams& k, int sms, int per_sm) {
     const long long ctas = (long long)((k.nx + kMarchW2 - 1) / kMarchW2) * ((k.ny + k.tz - 1) / k.tz);
     k.tile2d = sms > 0 && ctas < sms;
 }
+
+constexpr int kTmapStage = 0, kTmapPrefetch = 1;   // encode_tmap kinds
 
 const Ops* ops_d2_f64();
 const Ops* ops_d2_f32();

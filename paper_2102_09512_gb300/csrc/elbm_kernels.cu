@@ -921,16 +921,18 @@ fused3d_kernel(const __grid_constant__ KParams p, const __grid_constant__ DirPla
     // pref > 0: plane q's pulled source windows are prefetched into L2 `pref` planes
     // before their cp.async copies are issued (one tensor-prefetch box per direction,
     // issued by lanes of the last warp, which has no halo work), so that the copies of
-    // the plane buffer find their lines in L2.  The box for direction i covers the
-    // columns x0 - XO .. x0 + TX + XO - 1 (XO keeps its first column 16-byte aligned)
-    // and rows y0 - 1 - c_y .. y0 + TY - c_y of source plane q - c_z.
-    constexpr int XO = 16 / (int)sizeof(P);
+    // the plane buffer find their lines in L2.  The box for direction i (pmap: TX x TY+2
+    // pairs) covers the tile's own columns x0 .. x0 + TX - 1 and rows y0 - 1 - c_y ..
+    // y0 + TY - c_y of source plane q - c_z.  The columns the pulls take beyond the tile
+    // (x0 - 1 - c_x, x0 + TX - c_x) are left to the neighbouring tiles' boxes: a box
+    // widened to them must start on a 16-byte boundary and then carries whole lines of
+    // the neighbours' columns, which in FP32 cost 15 % more DRAM reads and 11 % of the step.
     const int pf_lane = tid - (NT - 32);
     auto prefetch_plane = [&](int q) {
         if (pf_lane >= 0 && pf_lane < Q) {
             const int i = pf_lane, b = (i / 3) % 3, c = i / 9;
-            // starts clamped to the tensor (x0 - XO stays a multiple of XO)
-            tma_prefetch_3d(&pmap, max(x0 - XO, 0), max(y0 - b, 0), i * p.nz + map_axis(q + 1 - c, p.nz, p.per_z));
+            // x0 is a multiple of TX (x0 * pair size a multiple of 16 bytes); rows clamped
+            tma_prefetch_3d(&pmap, x0, max(y0 - b, 0), i * p.nz + map_axis(q + 1 - c, p.nz, p.per_z));
         }
     };
 
@@ -1244,8 +1246,8 @@ fused3d_tma_kernel(const __grid_constant__ KParams p, const __grid_constant__ Di
     // prologue: Q~_zzz below the segment, planes zb and zb+1 in flight, moments of zb
     R qz_prev = R(0), qz_cur = R(0), qz_next = R(0);
     if (active) qz_prev = direct_anomaly_z<CAL>(p, src, x, y, map_axis(zb - 1, p.nz, p.per_z));
-    // L2 prefetch of the plane after the two in flight (as in fused3d_kernel), by lanes of
-    // the last warp
+    // L2 prefetch of the plane after the two in flight, by lanes of the last warp, one
+    // staging box per direction (ELBM_PREF_TMA, off by default)
     const int pf_lane = tid - (NT - 32);
     auto prefetch_plane = [&](int q) {
         if (kPrefTma && pf_lane >= 0 && pf_lane < Q) {
@@ -1740,8 +1742,10 @@ int tma_supported(const KParams& p) {
 }
 
 // Tensor map of a population store as rank 3: x (nx pairs), y (ny), w = i * nz + z (the
-// planes of all directions), box TmaCfg::BW x RB x 1.  The encoder is the driver's,
-// reached through the runtime (no link against the driver library).
+// planes of all directions); box TmaCfg::BW x RB x 1 (kTmapStage: the TMA-staged
+// kernel's copies) or TX x kTYP + 2 x 1 (kTmapPrefetch: the default pipelined kernel's
+// L2 prefetch of a tile's source rows).  The encoder is the driver's, reached through
+// the runtime (no link against the driver library).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -1754,13 +1758,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
 }
 
-int encode_tmap(const KParams& p, const void* base, CUtensorMap* out) {
-    if (!tma_supported(p)) return 0;
+int encode_tmap(const KParams& p, const void* base, CUtensorMap* out, int kind) {
+    if (!tma_supported(p) || (kind != kTmapStage && kind != kTmapPrefetch)) return 0;
     static const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();   // resolved once, thread-safe
     if (!encode) return -1;
     const cuuint64_t dims[3] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny, (cuuint64_t)p.nz * Q};
     const cuuint64_t strides[2] = {(cuuint64_t)p.nx * sizeof(P), (cuuint64_t)p.nx * p.ny * sizeof(P)};
-    const cuuint32_t box[3] = {(cuuint32_t)TmaCfg::BW, (cuuint32_t)TmaCfg::RB, 1u};
+    const cuuint32_t box[3] = {(cuuint32_t)(kind == kTmapStage ? TmaCfg::BW : TX),
+                               (cuuint32_t)(kind == kTmapStage ? TmaCfg::RB : kTYP + 2), 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     const CUtensorMapDataType dt = sizeof(P) == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
 #ifndef ELBM_TMAP_PROMO
@@ -1944,7 +1949,7 @@ cudaError_t launch_tma_cal(const KParams& p, const void* src, void* dst, const C
     }
 }
 
-// TMA-staged fused step; map is the tensor map of src (encode_tmap).
+// TMA-staged fused step; map is the tensor map of src (encode_tmap, kTmapStage).
 cudaError_t launch_fused_tma(const KParams& p, const void* src, void* dst, const CUtensorMap* map,
                              double* partials, int* nblocks, int* status, cudaStream_t s, long long* launches) {
     if (!tma_supported(p) || !map) return cudaErrorInvalidValue;
@@ -1979,7 +1984,8 @@ cudaError_t launch_fused_reread(const KParams& p, const void* src, void* dst, do
     return launch_fused<kD>(p, src, dst, partials, nblocks, status, s, launches, true);
 }
 
-// The default fused step with src's tensor map at hand (L2 prefetch of the planes ahead).
+// The default fused step with src's prefetch tensor map at hand (encode_tmap,
+// kTmapPrefetch: L2 prefetch of the planes ahead).
 cudaError_t launch_fused_pf(const KParams& p, const void* src, void* dst, const CUtensorMap* map, double* partials,
                             int* nblocks, int* status, cudaStream_t s, long long* launches) {
     return launch_fused<kD>(p, src, dst, partials, nblocks, status, s, launches, false, map);
