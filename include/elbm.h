@@ -158,8 +158,11 @@ int elbm_bytes_required(const elbm_handle *h, size_t *pop_bytes, size_t *aux_byt
 int elbm_bind(elbm_handle *h, void *pop_a, void *pop_b, void *aux, void *stream);
 
 /* Initial state f = f^eq(rho,u,T), g = g^eq(rho,u,T) (no non-equilibrium part).
- * _device: FP64 device arrays; plain: host arrays (copied through the aux staging
- * area, synchronising). */
+ * _device: FP64 device arrays; plain: host arrays, synchronising.  Host arrays in
+ * page-locked memory the device maps (cudaHostAlloc, cudaMallocHost, cudaHostRegister),
+ * each inside one allocation, are read by the initialisation kernel directly over the
+ * host link; other host memory is copied through the aux staging area.  The results
+ * are the same either way. */
 int elbm_set_fields(elbm_handle *h, const double *rho, const double *u, const double *T);
 int elbm_set_fields_device(elbm_handle *h, const double *rho, const double *u, const double *T);
 
@@ -167,7 +170,8 @@ int elbm_set_fields_device(elbm_handle *h, const double *rho, const double *u, c
 int elbm_step(elbm_handle *h, int nsteps);
 
 /* rho, u, T of the current state (Eqs. density, momentum, energy, E).
- * Plain: host arrays, synchronises and returns the latched device status.
+ * Plain: host arrays, synchronises and returns the latched device status (page-locked
+ * mapped host arrays are written by the field kernel directly, as for elbm_set_fields).
  * _device: FP64 device arrays, asynchronous. */
 int elbm_get_fields(elbm_handle *h, double *rho, double *u, double *T);
 int elbm_get_fields_device(elbm_handle *h, double *rho, double *u, double *T);
@@ -183,6 +187,16 @@ int elbm_conservation(elbm_handle *h, double out[5]);
  * thread updates) and per warp, FP64 across warps and CTAs (relative rounding of order
  * 1e-7, below that of the FP32 node values).  Synchronises. */
 int elbm_step_totals(elbm_handle *h, double out[5]);
+
+/* The same totals without synchronising: enqueues on the handle's stream the reduction
+ * of the last step's per-CTA sums and the copy of the five totals into out, and
+ * returns.  out must stay valid until the stream has passed that point (an event
+ * recorded after the call, cudaStreamSynchronize, or any synchronising call of this
+ * library); with out in page-locked host memory the copy is asynchronous too, so the
+ * caller can enqueue the next steps before reading the totals of this one.  The latched
+ * status is not read (the next synchronising call reports it).  ELBM_ERR_ARG before the
+ * first step. */
+int elbm_step_totals_async(elbm_handle *h, double out[5]);
 
 /* Turbulence statistics of the current state (paper Sec. III.D), volume averages
  * over all nodes, FP64: out = {<rho>, rho_rms, K = <rho u.u>/2, u_rms = sqrt(<u.u>/D),

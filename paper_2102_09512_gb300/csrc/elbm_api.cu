@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/elbm.h): parameter validation, buffer
 // binding, schedule selection and the host side of the diagnostics.  No kernel here
 // touches the populations except the small reduction finaliser.
+#include <cuda.h>   // driver types (CUpointer_attribute); the driver is reached through the runtime
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -66,31 +67,66 @@ const Ops* pick_ops(int D, int store) {
 // Compensated FP64 sum over nb partial vectors of `width` values (width <= kMaxWidth).
 constexpr int kMaxWidth = 12;   // widest partial vector: step totals 5, statistics kStatsSums
 static_assert(kStatsSums <= kMaxWidth, "finalize width");
+// The sum runs on kFinBlocks CTAs: CTA b takes a contiguous range of the partial vectors,
+// each thread a Neumaier sum of its share, the CTA a fixed pairwise tree of the threads'
+// (sum, compensation) pairs; the last CTA to finish (a counter in the auxiliary buffer,
+// zero between launches) adds the kFinBlocks pairs in order and writes the result.  The
+// order of every operation is fixed, so the result does not depend on the schedule.
+constexpr int kFinBlocks = 32;
+constexpr int kFinThreads = 128;
 
-__global__ void finalize_kernel(const double* __restrict__ partials, int nb, int width, double* __restrict__ out) {
+__device__ __forceinline__ void neumaier_add(double& s, double& c, double v) {
+    const double t = s + v;
+    c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+}
+
+__global__ void __launch_bounds__(kFinThreads)
+finalize_kernel(const double* __restrict__ partials, int nb, int width, double* __restrict__ scratch,
+                unsigned* __restrict__ count, double* __restrict__ out) {
+    const int tid = threadIdx.x;
     double s[kMaxWidth] = {}, c[kMaxWidth] = {};
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-        for (int k = 0; k < width; ++k) {   // Neumaier
-            const double v = partials[(size_t)width * j + k];
-            const double t = s[k] + v;
-            c[k] += fabs(s[k]) >= fabs(v) ? (s[k] - t) + v : (v - t) + s[k];
-            s[k] = t;
-        }
+    const int chunk = (nb + gridDim.x - 1) / gridDim.x;
+    const int j0 = blockIdx.x * chunk, j1 = min(j0 + chunk, nb);
+    for (int j = j0 + tid; j < j1; j += kFinThreads)
+        for (int k = 0; k < width; ++k) neumaier_add(s[k], c[k], partials[(size_t)width * j + k]);
+    __shared__ double rs[kMaxWidth][kFinThreads], rc[kMaxWidth][kFinThreads];
+    for (int k = 0; k < width; ++k) {
+        rs[k][tid] = s[k];
+        rc[k][tid] = c[k];
     }
-    __shared__ double red[kMaxWidth][256];
-    for (int k = 0; k < width; ++k) red[k][threadIdx.x] = s[k] + c[k];
     __syncthreads();
-    if (threadIdx.x < width) {   // fixed-order compensated sum of the 256 thread values
-        const int k = threadIdx.x;
-        double ss = 0.0, cc = 0.0;
-        for (int j = 0; j < 256; ++j) {
-            const double v = red[k][j];
-            const double t = ss + v;
-            cc += fabs(ss) >= fabs(v) ? (ss - t) + v : (v - t) + ss;
-            ss = t;
+    for (int w = kFinThreads / 2; w > 0; w /= 2) {   // pairs (s, c) + (s', c') -> (s + s', c + c' + error)
+        if (tid < w) {
+            for (int k = 0; k < width; ++k) {
+                double a = rs[k][tid], cc = rc[k][tid] + rc[k][tid + w];
+                neumaier_add(a, cc, rs[k][tid + w]);
+                rs[k][tid] = a;
+                rc[k][tid] = cc;
+            }
         }
-        out[k] = ss + cc;
+        __syncthreads();
     }
+    if (tid < width) {
+        scratch[2 * (kMaxWidth * blockIdx.x + tid)] = rs[tid][0];
+        scratch[2 * (kMaxWidth * blockIdx.x + tid) + 1] = rc[tid][0];
+    }
+    __threadfence();   // this CTA's pair is visible before its arrival is counted
+    __syncthreads();
+    __shared__ bool last;
+    if (tid == 0) last = atomicAdd(count, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (tid < width) {
+        double ss = 0.0, cc = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) {
+            neumaier_add(ss, cc, __ldcg(scratch + 2 * (kMaxWidth * b + tid)));
+            cc += __ldcg(scratch + 2 * (kMaxWidth * b + tid) + 1);
+        }
+        out[tid] = ss + cc;
+    }
+    if (tid == 0) *count = 0u;   // ready for the next launch on this stream
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? ELBM_OK : ELBM_ERR_CUDA; }
@@ -109,6 +145,10 @@ void compute_aux(elbm_handle* h) {
     off = align_up(off + sizeof(int));
     a.totals = off;
     off = align_up(off + kMaxWidth * sizeof(double));
+    a.fin_count = off;
+    off = align_up(off + sizeof(unsigned));
+    a.fin_scratch = off;
+    off = align_up(off + (size_t)2 * kMaxWidth * kFinBlocks * sizeof(double));
     a.partials = off;
     off = align_up(off + (5 + kStatsSums) * sizeof(double) * (size_t)a.max_blocks);
     a.qfield = off;
@@ -135,6 +175,44 @@ double* query_partials(elbm_handle* h) {
 }
 double* staging(elbm_handle* h) { return (double*)(h->auxp + h->aux.staging); }
 
+// Host fields in page-locked memory that the device maps (cudaHostAlloc, cudaMallocHost
+// or cudaHostRegister under unified addressing) are read and written by the field
+// kernels themselves, over the host link, with no staging copy.  mapped_host returns the
+// device address of such a buffer when [p, p + bytes) lies inside one allocation (the
+// driver's range attributes), else nullptr, and the transfer goes through the staging
+// area with cudaMemcpyAsync: a short or pageable buffer never reaches a kernel.
+using PointerAttrFn = CUresult (*)(void*, CUpointer_attribute, CUdeviceptr);
+PointerAttrFn pointer_attr_fn() {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+        cudaGetLastError();   // leave no sticky error behind
+        return nullptr;
+    }
+    return reinterpret_cast<PointerAttrFn>(fn);
+}
+
+const void* mapped_host(const void* p, size_t bytes) {
+    static const PointerAttrFn attr = pointer_attr_fn();   // resolved once, thread-safe
+    if (!attr || !p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    const CUdeviceptr dp = (CUdeviceptr)(uintptr_t)a.devicePointer;
+    CUdeviceptr start = 0;
+    size_t size = 0;
+    if (attr(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, dp) != CUDA_SUCCESS ||
+        attr(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, dp) != CUDA_SUCCESS)
+        return nullptr;
+    if (dp < start || bytes > size || dp - start > size - bytes) return nullptr;
+    return a.devicePointer;
+}
+
 // Synchronise, read and clear the latched device status.
 int sync_status(elbm_handle* h) {
     int st = 0;
@@ -150,14 +228,26 @@ int sync_status(elbm_handle* h) {
     return ELBM_OK;
 }
 
-int finalize_to_host(elbm_handle* h, const double* partials, int nb, double* out, int width = 5) {
-    finalize_kernel<<<1, 256, 0, h->stream>>>(partials, nb, width, totals_ptr(h));
+// Reduction of nb per-CTA partial sums into out (host memory), enqueued on the handle's
+// stream: written by the kernel itself when out is page-locked mapped memory, else
+// reduced into the totals slot and copied; finalize_to_host also synchronises and reads
+// the status.
+int finalize_async(elbm_handle* h, const double* partials, int nb, double* out, int width = 5) {
+    double* direct = (double*)mapped_host(out, (size_t)width * sizeof(double));
+    const int grid = nb < kFinBlocks ? (nb > 0 ? nb : 1) : kFinBlocks;
+    finalize_kernel<<<grid, kFinThreads, 0, h->stream>>>(partials, nb, width,
+                                                         (double*)(h->auxp + h->aux.fin_scratch),
+                                                         (unsigned*)(h->auxp + h->aux.fin_count),
+                                                         direct ? direct : totals_ptr(h));
     ++h->launches;
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !direct)
         e = cudaMemcpyAsync(out, totals_ptr(h), width * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-    if (e != cudaSuccess) return ELBM_ERR_CUDA;
-    return sync_status(h);
+    return e == cudaSuccess ? ELBM_OK : ELBM_ERR_CUDA;
+}
+int finalize_to_host(elbm_handle* h, const double* partials, int nb, double* out, int width = 5) {
+    const int rc = finalize_async(h, partials, nb, out, width);
+    return rc != ELBM_OK ? rc : sync_status(h);
 }
 
 }  // namespace
@@ -193,8 +283,8 @@ int elbm_create(const elbm_params* prm, elbm_handle** out) {
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
         {
-            if (D == 3) h->kp.tz = choose_tz(kp, h->ops->fused_tile_y, sms, h->ops->fused_occupancy(), kp.tz);
-            else plan_d2q9(h->kp, sms, h->ops->fused_occupancy());
+            if (D == 3) h->kp.tz = choose_tz(kp, h->ops->fused_tile_y, sms, h->ops->fused_occupancy(h->kp), kp.tz);
+            else plan_d2q9(h->kp, sms, h->ops->fused_occupancy(h->kp));
         }
         else
             cudaGetLastError();   // no device: keep the fallback, clear the error
@@ -236,7 +326,9 @@ int elbm_bind(elbm_handle* h, void* pop_a, void* pop_b, void* aux, void* stream)
     h->stream = (cudaStream_t)stream;
     h->cur = 0;
     h->bound = true;
-    return cuda_status(cudaMemsetAsync(status_ptr(h), 0, sizeof(int), h->stream));
+    cudaError_t e = cudaMemsetAsync(status_ptr(h), 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->auxp + h->aux.fin_count, 0, sizeof(unsigned), h->stream);
+    return cuda_status(e);
 }
 
 // AA: C(X_0) in layout L0 from equilibria already written in place (a step from layout L1
@@ -262,6 +354,16 @@ int elbm_set_fields_device(elbm_handle* h, const double* rho, const double* u, c
 
 int elbm_set_fields(elbm_handle* h, const double* rho, const double* u, const double* T) {
     if (!h || !h->bound || !rho || !u || !T) return ELBM_ERR_ARG;
+    {
+        const size_t b = (size_t)h->N * sizeof(double);
+        const double* dr = (const double*)mapped_host(rho, b);
+        const double* du = dr ? (const double*)mapped_host(u, (size_t)h->D * b) : nullptr;
+        const double* dT = du ? (const double*)mapped_host(T, b) : nullptr;
+        if (dT) {   // page-locked fields: the initialisation kernel reads them directly
+            const int rc = elbm_set_fields_device(h, dr, du, dT);
+            return rc != ELBM_OK ? rc : sync_status(h);
+        }
+    }
     if (h->layout == ELBM_LAYOUT_AA) {   // chunks of staging_nodes(h) nodes
         h->cur = 0;
         h->steps = 0;
@@ -345,6 +447,16 @@ int elbm_get_fields_device(elbm_handle* h, double* rho, double* u, double* T) {
 
 int elbm_get_fields(elbm_handle* h, double* rho, double* u, double* T) {
     if (!h || !h->bound || !rho || !u || !T) return ELBM_ERR_ARG;
+    {
+        const size_t b = (size_t)h->N * sizeof(double);
+        double* dr = (double*)mapped_host(rho, b);
+        double* du = dr ? (double*)mapped_host(u, (size_t)h->D * b) : nullptr;
+        double* dT = du ? (double*)mapped_host(T, b) : nullptr;
+        if (dT) {   // page-locked fields: the field kernel writes them directly
+            const int rc = elbm_get_fields_device(h, dr, du, dT);
+            return rc != ELBM_OK ? rc : sync_status(h);
+        }
+    }
     if (h->layout == ELBM_LAYOUT_AA) {   // chunks of staging_nodes(h) nodes
         const long long N = h->N, C = staging_nodes(h);
         const KParams k = diag_params(h);
@@ -421,6 +533,12 @@ int elbm_step_totals(elbm_handle* h, double out[5]) {
     if (!h || !h->bound || !out) return ELBM_ERR_ARG;
     if (h->steps == 0) return ELBM_ERR_ARG;
     return finalize_to_host(h, step_partials(h), h->step_blocks, out);
+}
+
+int elbm_step_totals_async(elbm_handle* h, double out[5]) {
+    if (!h || !h->bound || !out) return ELBM_ERR_ARG;
+    if (h->steps == 0) return ELBM_ERR_ARG;
+    return finalize_async(h, step_partials(h), h->step_blocks, out);
 }
 
 int elbm_set_kernel(elbm_handle* h, int kernel) {

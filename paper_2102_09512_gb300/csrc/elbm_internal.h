@@ -212,7 +212,9 @@ constexpr int kMarchSegs[3] = {32, 64, 128};
 // Layout of the auxiliary buffer (all offsets 256-byte aligned).
 struct AuxLayout {
     size_t status;      // int32 status word
-    size_t totals;      // 8 doubles: finalised totals
+    size_t totals;      // up to 12 doubles: finalised totals
+    size_t fin_count;   // uint32 arrival counter of the finalisation (zero between launches)
+    size_t fin_scratch; // per-CTA (sum, compensation) pairs of the finalisation
     size_t partials;    // max_blocks x 5 doubles: per-CTA totals
     size_t qfield;      // D x N values of Q~ (two-pass schedule), arithmetic type
     size_t staging;     // 5 x N doubles (host field transfers)
@@ -267,7 +269,9 @@ struct Ops {
     cudaError_t (*stats)(const KParams& p, const void* pop, double* partials, int* nblocks, cudaStream_t s,
                          long long* launches);   // kStatsSums partial sums per CTA
     int fused_tile_y;             // D3Q27: tile height of the fused kernels (tile width 32); D2Q9: 1 (row march)
-    int (*fused_occupancy)();     // resident CTAs per SM of the default fused D3Q27 kernel (0: unknown)
+    // resident CTAs per SM of the default fused kernel for the grid p (the D2Q9 march is
+    // compiled with and without fixed-state faces; 0: unknown)
+    int (*fused_occupancy)(const KParams& p);
     cudaError_t (*step_fused_tma)(const KParams& p, const void* src, void* dst, const CUtensorMap* src_map,
                                   double* partials, int* nblocks, int* status, cudaStream_t s, long long* launches);
     int (*tma_supported)(const KParams& p);   // the grid suits the TMA-staged D3Q27 kernel

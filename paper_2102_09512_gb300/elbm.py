@@ -69,6 +69,7 @@ _SIGS = {
     "elbm_get_fields_device": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "elbm_conservation": (ctypes.c_int, [_vp, _dp]),
     "elbm_step_totals": (ctypes.c_int, [_vp, _dp]),
+    "elbm_step_totals_async": (ctypes.c_int, [_vp, ctypes.c_void_p]),
     "elbm_turbulence_stats": (ctypes.c_int, [_vp, _dp]),
     "elbm_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int]),
     "elbm_set_layout": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -177,6 +178,12 @@ def elbm_conservation(h) -> np.ndarray:
     out = np.zeros(5)
     _check(lib().elbm_conservation(h, out.ctypes.data_as(_dp)), "elbm_conservation")
     return out
+
+
+def elbm_step_totals_async(h, out):
+    """Enqueues the step totals' copy into out (a 5-element FP64 host tensor or array,
+    page-locked for an asynchronous copy); returns the status code."""
+    return lib().elbm_step_totals_async(h, _ptr(out))
 
 
 def elbm_step_totals(h) -> np.ndarray:
