@@ -271,6 +271,27 @@ def time_store(E, torch, case, store, steps, warmup, stream, kernel=0, windows=1
     return out, (g.launches - l0) // windows, g, rc
 
 
+def reduced_store_errors(E, torch, case, stream, finals):
+    """Relative L2 norms (rho, u, T) of each reduced-precision store's fields at the end of
+    its bench window against an FP64 run of the same workload over the same number of
+    steps (one FP64 run, stepped to each store's count in turn)."""
+    import numpy as np
+    out = {}
+    g = E.Solver.from_case(case, store="f64", stream=stream)
+    done = 0
+    try:
+        for steps, store in sorted((v[0], s) for s, v in finals.items()):
+            g.step(steps - done)
+            done = steps
+            ref = g.fields()
+            out[store] = {"steps": steps, **{name: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+                                              for name, a, b in zip(("rho", "u", "T"), finals[store][1], ref)}}
+    except E.ElbmError as err:
+        out = {s: {"error": str(err)} for s in finals}
+    g.close()
+    return out
+
+
 def time_e2e(E, torch, case, store, steps, stream):
     """End-to-end through the C ABI with host buffers: upload the initial fields from
     pinned host memory, take `steps` steps reading each step's conserved totals back to
@@ -449,6 +470,8 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-d2q9", action="store_true")
     ap.add_argument("--no-aa", action="store_true")
+    ap.add_argument("--no-store-error", action="store_true",
+                    help="skip the FP64 run that measures the reduced stores' error at the end of their windows")
     ap.add_argument("--windows", type=int, default=5,
                     help="back-to-back timed windows of --steps steps for the headline store (median reported)")
     ap.add_argument("--size", type=int, default=N_SIDE, help="box side (the bench workload is 256)")
@@ -486,9 +509,10 @@ def main():
     head = None
     clocks = None
     launches_head = None
+    finals = {}
     for store in stores:
-        # The headline FP32 store is timed over exactly --steps.  The FP64 store is 50x
-        # slower and is timed over a quarter of them.  The reduced-precision stores are
+        # The headline FP32 store is timed over exactly --steps.  The FP64 store is about
+        # 18x slower and is timed over a quarter of them.  The reduced-precision stores are
         # timed over at most 20 steps after at most 5 warm-up steps (FP16 deviations) and
         # 10 after 3 (BF16): on this workload their rounding tips the flow over the
         # scheme's stability edge after about 30 and 20 steps, while FP32 and FP64 stay
@@ -527,6 +551,9 @@ def main():
             totals = g.conservation()
         except E.ElbmError:
             totals = [float("nan")] * 5
+        if store in STORE_NOTES and rank == 0 and not args.no_store_error:
+            # the reduced store's state at the end of its window, for the error against FP64
+            finals[store] = (warm + windows * k, g.fields())
         g.close()
         del g
         torch.cuda.empty_cache()
@@ -550,6 +577,11 @@ def main():
         if head is None and "error" not in variants[store]:
             head = store
             launches_head = launches
+    if finals:
+        for store, err in reduced_store_errors(E, torch, case, stream, finals).items():
+            variants[store]["rel_l2_vs_fp64_at_window_end"] = err
+        finals.clear()
+        torch.cuda.empty_cache()
     hs = variants[head]
     if rank != 0:
         dist.barrier() if ws > 1 else None
