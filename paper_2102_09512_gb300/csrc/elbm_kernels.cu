@@ -586,8 +586,15 @@ __global__ void aa_moments_kernel(const __grid_constant__ KParams p, P* A, R* __
 
 // Pass 2 of an AA step: the same reads, the derivative of Q~ from the field, collision, and
 // the writes into the slots just read.
+// Two CTAs per SM (at most 128 registers) for the FP32-arithmetic stores: the L0 form holds
+// the pull offsets for its pushed writes and would take 156 (FP32) / 182 (FP16) registers,
+// one CTA of 8 warps per SM, which made it twice as slow as the L1 form (AA step at 256^3,
+// FP32 6.1 -> 7.8 GLUPS, FP16 7.6 -> 10.7 with the cap, despite about 100 bytes of spills).
+// FP64 keeps one CTA (the cap would spill 0.8 KB per thread).
+constexpr int kAaMinBlocks = sizeof(R) == 4 ? 2 : 1;
 template <bool FROM_L1>
-__global__ void aa_collide_kernel(const __grid_constant__ KParams p, P* A, const R* __restrict__ qf,
+__global__ void __launch_bounds__(kThreads1D, kAaMinBlocks)
+aa_collide_kernel(const __grid_constant__ KParams p, P* A, const R* __restrict__ qf,
                                   double* __restrict__ partials, int* __restrict__ status) {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     R tot[5] = {0, 0, 0, 0, 0};

@@ -3,11 +3,16 @@ layout alternating with the step parity, on the two-pass schedule, for periodic 
 
 The AA kernels run the same per-node arithmetic as the ping-pong two-pass kernels
 (moments, Q~ field, collision) and differ only in where each pair is read and written.
-With the FP32-arithmetic stores (FP32, FP16 and BF16 deviations) the fields, totals and
-statistics after any number of steps are bit for bit those of the two-pass ping-pong
-schedule; with the FP64 store the compiler contracts a few multiply-adds of the two
-kernels differently, and they agree to the last bits (1e-14 relative).  Against the FP64
-oracle they meet the parity bounds.
+They are compiled under different register budgets (the D3Q27 AA collision is held to two
+CTAs per SM), and the compiler contracts a different set of multiply-adds into fused ones,
+so the D3Q27 results agree to the rounding of the arithmetic rather than bit for bit (the
+D2Q9 FP32-arithmetic ones stay bit for bit; FP64 differs in the last bits on both lattices):
+FP64 to 1e-14 relative L2, FP32 to 5e-6 after 20 steps (measured 7.8e-7).  The 16-bit
+stores round every pair to 16 bits after each step, and a few-ulp FP32 difference now and
+then lands a pair on the other side of a 16-bit rounding boundary; those flips grow with
+the steps (measured after 20 steps: FP16 3.2e-4, BF16 2.2e-3), so the two schedules are
+held to each other by the stores' parity bounds against the oracle (1e-3, 8e-3).  Against
+the FP64 oracle every schedule meets those bounds.
 """
 import numpy as np
 import pytest
@@ -18,6 +23,8 @@ from paper_2102_09512_gb300 import cases as C
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-12, "f32": 1e-5, "f16dev": 1e-3}
+# AA against ping-pong two-pass, relative L2 (see the module docstring)
+SAME = {"f64": 1e-14, "f32": 5e-6, "f16dev": 1e-3, "bf16dev": 8e-3}
 U0 = (0.09, -0.07, 0.06)
 
 
@@ -54,14 +61,15 @@ def pair(E, c, store):
 def test_aa_equals_pingpong_twopass(E, D, store):
     """After 0, 1, 2, 7 and 20 steps (both layouts, in either order) the fields, the FP64
     totals, the step totals and the turbulence statistics equal the ping-pong two-pass
-    schedule's (bit for bit; FP64 to 1e-14)."""
+    schedule's to the rounding of the arithmetic (SAME; D2Q9 FP32-arithmetic stores bit for
+    bit)."""
     c = CASES[D]()
     aa, pp = pair(E, c, store)
 
     def same(a, b):
-        if store == "f64":
-            return rel_l2(a, b) <= 1e-14
-        return np.array_equal(a, b)
+        if D == 2 and store != "f64":
+            return np.array_equal(a, b)
+        return rel_l2(a, b) <= SAME[store]
 
     done = 0
     for k in (0, 1, 2, 7, 20):
@@ -118,7 +126,7 @@ def test_aa_checkpoint_restart(E):
 
 def test_aa_power_law_caloric_and_central(E):
     """The options of the collision (power-law viscosity, cubic Cv(T), central derivative)
-    on the AA layout give the ping-pong two-pass results (FP32 bit for bit)."""
+    on the AA layout give the ping-pong two-pass results (to the rounding of the arithmetic)."""
     c = C.random_smooth(3, 24, 17, 10, seed=143, mu0=0.01, mu_exp=0.76, dT=0.04, du=0.05, u0=U0)
     c.cv = (1.0, 4.0, -4.0, 5.0)
     for store in ("f64", "f32"):
@@ -128,7 +136,7 @@ def test_aa_power_law_caloric_and_central(E):
         aa.step(9)
         pp.step(9)
         for x, y in zip(aa.fields(), pp.fields()):
-            assert (rel_l2(x, y) <= 1e-14) if store == "f64" else np.array_equal(x, y), store
+            assert rel_l2(x, y) <= SAME[store], store
         aa.close()
         pp.close()
 
@@ -142,7 +150,7 @@ def test_aa_chunked_host_transfers(E):
     aa.step(3)
     pp.step(3)
     for x, y in zip(aa.fields(), pp.fields()):
-        assert np.array_equal(x, y)
+        assert np.array_equal(x, y)   # D2Q9: the same compiled arithmetic
     aa.close()
     pp.close()
     torch.cuda.empty_cache()
