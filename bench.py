@@ -380,6 +380,35 @@ def d2q9_measure(E, torch, steps, warmup=3, side=4096):
     return out
 
 
+def sod_measure(E, torch, steps=500, warmup=10, group=50):
+    """The Sod shock tube (D2Q9 800 x 4, FP64, 500 steps; paper Sec. III.B), a grid of 3,200
+    nodes whose step costs little more than its launch: microseconds per step with one
+    launch per step and with groups of `group` steps replayed from a CUDA graph."""
+    from paper_2102_09512_gb300 import cases as C
+    c = C.sod()
+    out = {"grid": [c.nx, c.ny], "store": "f64", "steps": steps, "graph_group": group}
+    stream = torch.cuda.current_stream()
+    for name, g_steps in (("single_launches", 0), ("graph_replays", group)):
+        try:
+            g = E.Solver.from_case(c, store="f64", stream=stream)
+            g.set_step_graph(g_steps)
+            g.step(warmup)
+            g.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            g.sync()
+            g.close()
+        except E.ElbmError as err:
+            out[name] = {"error": str(err)}
+            continue
+        us = 1e3 * e0.elapsed_time(e1) / steps
+        out[name] = {"us_per_step": us, "mlups": c.N / us}
+    return out
+
+
 def aa_measure(E, torch, case, steps, warmup=3):
     """The single-store (AA) layout on the bench workload: the two-pass schedule updating one
     store in place (half the population memory), against the two-pass schedule on ping-pong
@@ -604,6 +633,10 @@ def main():
     if not args.no_aa:
         aa = aa_measure(E, torch, case, args.steps)
 
+    sod = None
+    if not args.no_d2q9:
+        sod = sod_measure(E, torch)
+
     ens = None
     if not args.no_ensemble:
         ens = ensemble_measure(E, torch, args.steps)
@@ -634,6 +667,7 @@ def main():
                    "parallelism": "replicas" if ws > 1 else "single-gpu"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_head,
         "clocks": clocks, "variants": variants, "ensemble": ens, "d2q9": d2q9, "aa_layout": aa,
+        "sod_800x4": sod,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:

@@ -169,6 +169,17 @@ int elbm_set_fields_device(elbm_handle *h, const double *rho, const double *u, c
 /* Advances nsteps time steps with the selected kernel schedule (asynchronous). */
 int elbm_step(elbm_handle *h, int nsteps);
 
+/* Steps replayed from CUDA graphs (for grids small enough that launching is what a step
+ * costs): with steps_per_graph = G > 0, elbm_step runs whole groups of G steps as one
+ * replay each of a graph captured on first use (one per starting store, or AA layout
+ * parity) and the remainder as single steps.  The replays launch the same kernels with
+ * the same arguments as single steps, so the results are the same.  The graphs hold the
+ * bound buffers, the kernel schedule and the kernel parameters; elbm_bind, elbm_set_kernel,
+ * elbm_set_tile_z and elbm_inject_wait_timeout drop them.  G = 0 (the default) turns
+ * replays off; G must be even (a replay ends at the parity it began) and at most 1024,
+ * else ELBM_ERR_ARG.  Not for use while the caller captures the handle's stream itself. */
+int elbm_set_step_graph(elbm_handle *h, int steps_per_graph);
+
 /* rho, u, T of the current state (Eqs. density, momentum, energy, E).
  * Plain: host arrays, synchronises and returns the latched device status (page-locked
  * mapped host arrays are written by the field kernel directly, as for elbm_set_fields).

@@ -35,6 +35,18 @@ struct elbm_handle {
     int step_blocks;         // CTAs that wrote step partials in the last step
     long long steps;
     long long launches;
+    // CUDA graphs of graph_steps steps (0: off), one per starting store / layout parity;
+    // dropped whenever a pointer, the kernel choice or a kernel parameter changes
+    int graph_steps = 0;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    long long graph_launches = 0;   // kernel launches one replay issues
+    void drop_graphs() {
+        for (auto& g : gexec) {
+            if (g) cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    }
+    ~elbm_handle() { drop_graphs(); }
 };
 
 namespace {
@@ -250,6 +262,70 @@ int finalize_to_host(elbm_handle* h, const double* partials, int nb, double* out
     return rc != ELBM_OK ? rc : sync_status(h);
 }
 
+// One step enqueued on stream st from the handle's current state; advances the store
+// index and the step count.
+cudaError_t step_one(elbm_handle* h, cudaStream_t st) {
+    cudaError_t e;
+    if (h->layout == ELBM_LAYOUT_AA) {   // the layout alternates: L0 after an even number of steps
+        e = h->ops->step_aa(h->kp, h->pop[0], h->auxp + h->aux.qfield, step_partials(h), &h->step_blocks,
+                            status_ptr(h), st, &h->launches, (int)(h->steps % 2));
+        if (e == cudaSuccess) ++h->steps;
+        return e;
+    }
+    const void* src = h->pop[h->cur];
+    void* dst = h->pop[1 - h->cur];
+    if (h->kernel == ELBM_KERNEL_TWOPASS)
+        e = h->ops->step_twopass(h->kp, src, dst, h->auxp + h->aux.qfield, step_partials(h), &h->step_blocks,
+                                 status_ptr(h), st, &h->launches);
+    else if (h->kernel == ELBM_KERNEL_FUSED_REREAD)
+        e = h->ops->step_fused_reread(h->kp, src, dst, step_partials(h), &h->step_blocks, status_ptr(h), st,
+                                      &h->launches);
+    else if (h->kernel == ELBM_KERNEL_FUSED_TMA)
+        e = h->tmap_ready ? h->ops->step_fused_tma(h->kp, src, dst, &h->tmap[h->cur], step_partials(h),
+                                                   &h->step_blocks, status_ptr(h), st, &h->launches)
+                          : cudaErrorNotSupported;
+    else if (h->tmap_ready)
+        e = h->ops->step_fused_pf(h->kp, src, dst, &h->pfmap[h->cur], step_partials(h), &h->step_blocks,
+                                  status_ptr(h), st, &h->launches);
+    else
+        e = h->ops->step_fused(h->kp, src, dst, step_partials(h), &h->step_blocks, status_ptr(h), st, &h->launches);
+    if (e == cudaSuccess) {
+        h->cur = 1 - h->cur;
+        ++h->steps;
+    }
+    return e;
+}
+
+// The parity a graph starts from: the store holding the state (ping-pong) or the layout of
+// the step parity (AA).  A graph of an even number of steps ends at the parity it began.
+int graph_parity(const elbm_handle* h) { return h->layout == ELBM_LAYOUT_AA ? (int)(h->steps % 2) : h->cur; }
+
+// Captures graph_steps steps from the current parity on a private stream; the handle's
+// state is restored afterwards (the replays advance it).
+cudaError_t build_step_graph(elbm_handle* h, cudaGraphExec_t* out) {
+    cudaStream_t cap;
+    cudaError_t err = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (err != cudaSuccess) return err;
+    const int cur = h->cur;
+    const long long steps = h->steps, launches = h->launches;
+    cudaGraph_t g = nullptr;
+    err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (err == cudaSuccess) {
+        cudaError_t le = cudaSuccess;
+        for (int k = 0; k < h->graph_steps && le == cudaSuccess; ++k) le = step_one(h, cap);
+        h->graph_launches = h->launches - launches;
+        err = cudaStreamEndCapture(cap, &g);
+        if (err == cudaSuccess) err = le;
+    }
+    h->cur = cur;
+    h->steps = steps;
+    h->launches = launches;
+    if (err == cudaSuccess) err = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    return err;
+}
+
 }  // namespace
 
 extern "C" {
@@ -314,6 +390,7 @@ int elbm_bind(elbm_handle* h, void* pop_a, void* pop_b, void* aux, void* stream)
         return ELBM_ERR_ARG;
     }
     if (((uintptr_t)pop_a | (uintptr_t)pop_b | (uintptr_t)aux) % kAlign) return ELBM_ERR_ARG;
+    h->drop_graphs();
     h->pop[0] = pop_a;
     h->pop[1] = pop_b;
     h->tmap_ready = false;
@@ -401,41 +478,27 @@ int elbm_set_fields(elbm_handle* h, const double* rho, const double* u, const do
 
 int elbm_step(elbm_handle* h, int nsteps) {
     if (!h || !h->bound || nsteps < 0) return ELBM_ERR_ARG;
-    if (h->layout == ELBM_LAYOUT_AA) {   // the layout alternates: L0 after an even number of steps
-        for (int s = 0; s < nsteps; ++s) {
-            const cudaError_t e = h->ops->step_aa(h->kp, h->pop[0], h->auxp + h->aux.qfield, step_partials(h),
-                                                  &h->step_blocks, status_ptr(h), h->stream, &h->launches,
-                                                  (int)(h->steps % 2));
+    if (h->kernel == ELBM_KERNEL_FUSED_TMA && !h->tmap_ready) return ELBM_ERR_UNSUPPORTED;
+    int s = 0;
+    if (h->graph_steps > 0) {   // whole groups of graph_steps steps, each one graph replay
+        for (; s + h->graph_steps <= nsteps; s += h->graph_steps) {
+            cudaGraphExec_t& g = h->gexec[graph_parity(h)];
+            cudaError_t e = g ? cudaSuccess : build_step_graph(h, &g);
+            if (e == cudaSuccess) e = cudaGraphLaunch(g, h->stream);
             if (e != cudaSuccess) return ELBM_ERR_CUDA;
-            ++h->steps;
+            h->steps += h->graph_steps;   // an even count: the store index is where it was
+            h->launches += h->graph_launches;
         }
-        return ELBM_OK;
     }
-    for (int s = 0; s < nsteps; ++s) {
-        const void* src = h->pop[h->cur];
-        void* dst = h->pop[1 - h->cur];
-        cudaError_t e;
-        if (h->kernel == ELBM_KERNEL_TWOPASS)
-            e = h->ops->step_twopass(h->kp, src, dst, h->auxp + h->aux.qfield, step_partials(h), &h->step_blocks,
-                                     status_ptr(h), h->stream, &h->launches);
-        else if (h->kernel == ELBM_KERNEL_FUSED_REREAD)
-            e = h->ops->step_fused_reread(h->kp, src, dst, step_partials(h), &h->step_blocks, status_ptr(h),
-                                          h->stream, &h->launches);
-        else if (h->kernel == ELBM_KERNEL_FUSED_TMA) {
-            if (!h->tmap_ready) return ELBM_ERR_UNSUPPORTED;
-            e = h->ops->step_fused_tma(h->kp, src, dst, &h->tmap[h->cur], step_partials(h), &h->step_blocks,
-                                       status_ptr(h), h->stream, &h->launches);
-        }
-        else if (h->tmap_ready)
-            e = h->ops->step_fused_pf(h->kp, src, dst, &h->pfmap[h->cur], step_partials(h), &h->step_blocks,
-                                      status_ptr(h), h->stream, &h->launches);
-        else
-            e = h->ops->step_fused(h->kp, src, dst, step_partials(h), &h->step_blocks, status_ptr(h), h->stream,
-                                   &h->launches);
-        if (e != cudaSuccess) return ELBM_ERR_CUDA;
-        h->cur = 1 - h->cur;
-        ++h->steps;
-    }
+    for (; s < nsteps; ++s)
+        if (step_one(h, h->stream) != cudaSuccess) return ELBM_ERR_CUDA;
+    return ELBM_OK;
+}
+
+int elbm_set_step_graph(elbm_handle* h, int steps_per_graph) {
+    if (!h || steps_per_graph < 0 || steps_per_graph > 1024 || steps_per_graph % 2) return ELBM_ERR_ARG;
+    h->drop_graphs();
+    h->graph_steps = steps_per_graph;
     return ELBM_OK;
 }
 
@@ -548,6 +611,7 @@ int elbm_set_kernel(elbm_handle* h, int kernel) {
     if (kernel == ELBM_KERNEL_FUSED_TMA && !h->ops->tma_supported(h->kp)) return ELBM_ERR_UNSUPPORTED;
     if (h->layout == ELBM_LAYOUT_AA && kernel != ELBM_KERNEL_TWOPASS) return ELBM_ERR_UNSUPPORTED;
     h->kernel = kernel;
+    h->drop_graphs();
     return ELBM_OK;
 }
 
@@ -569,6 +633,7 @@ int elbm_set_tile_z(elbm_handle* h, int tz) {
     if (h->ops->max_blocks(k) > h->aux.max_blocks) return ELBM_ERR_ARG;   // partials would not fit
     h->kp.tz = k.tz;
     h->kp.tile2d = 0;
+    h->drop_graphs();
     return ELBM_OK;
 }
 
@@ -594,6 +659,7 @@ int elbm_sync(elbm_handle* h) {
 int elbm_inject_wait_timeout(elbm_handle* h, int on) {
     if (!h || (on != 0 && on != 1)) return ELBM_ERR_ARG;
     h->kp.inject_tx = on ? 16u : 0u;
+    h->drop_graphs();
     return ELBM_OK;
 }
 

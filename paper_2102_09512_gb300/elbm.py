@@ -70,6 +70,7 @@ _SIGS = {
     "elbm_conservation": (ctypes.c_int, [_vp, _dp]),
     "elbm_step_totals": (ctypes.c_int, [_vp, _dp]),
     "elbm_step_totals_async": (ctypes.c_int, [_vp, ctypes.c_void_p]),
+    "elbm_set_step_graph": (ctypes.c_int, [_vp, ctypes.c_int]),
     "elbm_turbulence_stats": (ctypes.c_int, [_vp, _dp]),
     "elbm_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int]),
     "elbm_set_layout": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -178,6 +179,10 @@ def elbm_conservation(h) -> np.ndarray:
     out = np.zeros(5)
     _check(lib().elbm_conservation(h, out.ctypes.data_as(_dp)), "elbm_conservation")
     return out
+
+
+def elbm_set_step_graph(h, steps_per_graph: int):
+    return lib().elbm_set_step_graph(h, int(steps_per_graph))
 
 
 def elbm_step_totals_async(h, out):
@@ -400,6 +405,9 @@ class Solver:
 
     def step(self, n: int = 1):
         _check(elbm_step(self.h, n), "elbm_step")
+
+    def set_step_graph(self, steps_per_graph: int):
+        _check(elbm_set_step_graph(self.h, steps_per_graph), "elbm_set_step_graph")
 
     def fields(self):
         """(rho (N,), u (D, N), T (N,)) as numpy FP64 (synchronises)."""

@@ -187,3 +187,15 @@ def test_aa_layout_host_checks(L):
     assert aux < 3 * n * 4 + (5 * 8 << 25) + (1 << 30)
     assert pop + aux < 260e9 < 2 * pp_pop
     L.elbm_destroy(h)
+
+
+def test_step_graph_host_checks(L):
+    """Graph-replayed steps: an even group size of at most 1024 (0 turns replays off);
+    nothing is captured before the handle is bound (no CUDA call here)."""
+    h = L.elbm_create(L.make_params(2, 800, 4, 1, store="f64"))
+    for bad in (-2, 1, 3, 1026):
+        assert L.lib().elbm_set_step_graph(h, bad) == L.ELBM_ERR_ARG
+    for ok in (0, 2, 8, 1024):
+        assert L.lib().elbm_set_step_graph(h, ok) == L.ELBM_OK
+    assert L.lib().elbm_step(h, 4) == L.ELBM_ERR_ARG   # not bound
+    L.elbm_destroy(h)
