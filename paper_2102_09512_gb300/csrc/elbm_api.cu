@@ -360,7 +360,7 @@ int elbm_create(const elbm_params* prm, elbm_handle** out) {
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
         {
             if (D == 3) h->kp.tz = choose_tz(kp, h->ops->fused_tile_y, sms, h->ops->fused_occupancy(h->kp), kp.tz);
-            else plan_d2q9(h->kp, sms, h->ops->fused_occupancy(h->kp));
+            else plan_d2q9(h->kp, sms, h->ops->fused_occupancy(h->kp), h->ops->march_width);
         }
         else
             cudaGetLastError();   // no device: keep the fallback, clear the error

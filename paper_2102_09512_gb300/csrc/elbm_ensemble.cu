@@ -279,7 +279,7 @@ int elbm_ensemble_bind(elbm_ensemble* e, void* pop_a, void* pop_b, void* aux, vo
     e->bound = true;
     // the one-launch-per-instance mode runs each instance as a single lattice would on this device
     const int sms = sm_count();
-    for (KParams& k : e->kp) plan_d2q9(k, sms, e->ops->fused_occupancy(k));
+    for (KParams& k : e->kp) plan_d2q9(k, sms, e->ops->fused_occupancy(k), e->ops->march_width);
     cudaError_t c = cudaMemsetAsync(e->status(), 0, sizeof(int), e->stream);
     if (c == cudaSuccess)
         c = cudaMemcpyAsync(e->aux + e->a_params, e->kp.data(), e->kp.size() * sizeof(KParams),

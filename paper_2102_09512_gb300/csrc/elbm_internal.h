@@ -293,6 +293,7 @@ struct Ops {
     // pushed writes)
     cudaError_t (*step_aa)(const KParams& p, void* A, void* qfield, double* partials, int* nblocks, int* status,
                            cudaStream_t s, long long* launches, int from_l1);
+    int march_width;   // D2Q9: strip width of the single-lattice row march of this store
 };
 
 // z-segment length of the fused D3Q27 kernels.  Each CTA marches one (tile, segment)
@@ -325,17 +326,17 @@ inline int choose_tz(const KParams& k, int ty, int sms, int per_sm, int fallback
     const double tiles = (double)((k.nx + 31) / 32) * (double)((k.ny + ty - 1) / ty);
     return choose_segment(tiles, k.nz, sms, per_sm, fallback);
 }
-// The same choice for the D2Q9 row march: strips of kMarchW2 nodes, segments of rows.
-inline int choose_rows(const KParams& k, int sms, int per_sm, int fallback) {
-    return choose_segment((double)((k.nx + kMarchW2 - 1) / kMarchW2), k.ny, sms, per_sm, fallback);
+// The same choice for the D2Q9 row march: strips of `width` nodes, segments of rows.
+inline int choose_rows(const KParams& k, int sms, int per_sm, int fallback, int width) {
+    return choose_segment((double)((k.nx + width - 1) / width), k.ny, sms, per_sm, fallback);
 }
 // D2Q9 schedule for a device of `sms` SMs: the row segment, and whether the grid is too
 // small for the march (fewer strips x segments than SMs), in which case the default fused
 // schedule runs the one-tile-per-CTA kernel instead.  Without device information the
 // march with the fallback segment is kept.
-inline void plan_d2q9(KParams& k, int sms, int per_sm) {
-    k.tz = choose_rows(k, sms, per_sm, k.tz);
-    const long long ctas = (long long)((k.nx + kMarchW2 - 1) / kMarchW2) * ((k.ny + k.tz - 1) / k.tz);
+inline void plan_d2q9(KParams& k, int sms, int per_sm, int width) {
+    k.tz = choose_rows(k, sms, per_sm, k.tz, width);
+    const long long ctas = (long long)((k.nx + width - 1) / width) * ((k.ny + k.tz - 1) / k.tz);
     k.tile2d = sms > 0 && ctas < sms;
 }
 

@@ -1716,6 +1716,15 @@ constexpr int kW2 = kMarchW2;            // D2Q9 row march: strips of kW2 nodes
 #endif
 constexpr int kNBM = ELBM_MARCH_NB;      // row buffers of the march (2: one row in flight, 3: two)
 using MarchCfg = March2<kW2, kNBM>;
+// Strip width of the single-lattice D2Q9 march: 256 nodes for the 16-bit stores, whose
+// march is issue-bound and pays for the strip's two halo nodes half as often per node
+// (FP16 at 4096^2: 52.8 -> 55.2 GLUPS), kW2 for FP32 and FP64, which are bandwidth-bound
+// (256 measured 39.2 against 44.9 GLUPS in FP32).  The persistent ensemble keeps kW2.
+#ifndef ELBM_MARCH_W16
+#define ELBM_MARCH_W16 256
+#endif
+constexpr int kW2L = sizeof(P) == 4 ? ELBM_MARCH_W16 : kW2;
+using MarchCfgL = March2<kW2L, kNBM>;
 #ifndef ELBM_TY3
 #define ELBM_TY3 8
 #endif
@@ -1813,7 +1822,7 @@ DirPlanes dir_planes(const KParams& p, const void* src, void* dst) {
 // Grid of the default fused kernel: D2Q9 row march (strips x row segments of p.tz rows),
 // D3Q27 pipelined kernel (32 x kTYP column tiles x z segments of p.tz planes).
 dim3 fused_grid(const KParams& p) {
-    if (kD == 2) return dim3((p.nx + kW2 - 1) / kW2, (p.ny + p.tz - 1) / p.tz, 1);
+    if (kD == 2) return dim3((p.nx + kW2L - 1) / kW2L, (p.ny + p.tz - 1) / p.tz, 1);
     const int ty = kPipe ? kTYP : kTY3;
     return dim3((p.nx + TX - 1) / TX, (p.ny + ty - 1) / ty, (p.nz + p.tz - 1) / p.tz);
 }
@@ -1922,12 +1931,12 @@ cudaError_t launch_fused_cal(const KParams& p, const void* src, void* dst, doubl
             fused2d_kernel<kTY2, CAL><<<tile2d_grid(p), dim3(TX, kTY2), 0, s>>>(p, (const P*)src, (P*)dst, partials,
                                                                                status);
         } else {
-            auto kern = p.has_fixed ? march2d_kernel<kW2, kNBM, CAL, true> : march2d_kernel<kW2, kNBM, CAL, false>;
+            auto kern = p.has_fixed ? march2d_kernel<kW2L, kNBM, CAL, true> : march2d_kernel<kW2L, kNBM, CAL, false>;
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)MarchCfg::smem_bytes);
+                                                 (int)MarchCfgL::smem_bytes);
             if (e != cudaSuccess) return e;
             DirPlanes pl = dir_planes(p, src, dst);
-            kern<<<grid, kW2, MarchCfg::smem_bytes, s>>>(p, pl, (const P*)src, partials, status);
+            kern<<<grid, kW2L, MarchCfgL::smem_bytes, s>>>(p, pl, (const P*)src, partials, status);
         }
     } else {
         bool launched = false;
@@ -2108,10 +2117,10 @@ int fused_occupancy_impl(const KParams& p) {
             cudaSuccess)
             return 0;
     } else {
-        auto kern = p.has_fixed ? march2d_kernel<kW2, kNBM, false, true> : march2d_kernel<kW2, kNBM, false, false>;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg::smem_bytes) !=
+        auto kern = p.has_fixed ? march2d_kernel<kW2L, kNBM, false, true> : march2d_kernel<kW2L, kNBM, false, false>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfgL::smem_bytes) !=
                 cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kW2, MarchCfg::smem_bytes) != cudaSuccess)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kW2L, MarchCfgL::smem_bytes) != cudaSuccess)
             return 0;
     }
     return n;
@@ -2122,7 +2131,7 @@ const Ops kOps = {kD,          kST,           sizeof(P) / 2,  sizeof(R),        
                   launch_init, launch_fields, launch_twopass, launch_fused_default, launch_fused_reread,
                   launch_totals, launch_ensemble, ensemble_occupancy, launch_stats,
                   kD == 3 ? (kPipe ? kTYP : kTY3) : 1, fused_occupancy, launch_fused_tma, tma_supported, encode_tmap,
-                  launch_fused_pf, launch_init_nodes, launch_fields_nodes, launch_step_aa};
+                  launch_fused_pf, launch_init_nodes, launch_fields_nodes, launch_step_aa, kW2L};
 
 }  // namespace
 

@@ -126,11 +126,13 @@ MARCH_2D = {
 
 @pytest.mark.parametrize("tz", [1, 2, 7, 16, None])
 @pytest.mark.parametrize("case,store", [("periodic", "f64"), ("periodic", "f32"), ("periodic", "f16dev"),
-                                        ("zerograd", "f64"), ("zerograd", "f32"), ("periodic-zm", "f64")])
+                                        ("zerograd", "f64"), ("zerograd", "f32"), ("zerograd", "f16dev"),
+                                        ("periodic-zm", "f64")])
 def test_d2q9_row_march_segments(E, case, store, tz):
-    """The D2Q9 row march over grids of several 128-node strips (the last one ragged) and
-    row segments of 1, 2, 7 and 16 rows or the length chosen for the device, 100 steps:
-    segments of one and two rows run only the prologue and the last-row paths."""
+    """The D2Q9 row march over grids of several strips (128 nodes for FP64 and FP32, 256
+    for the 16-bit stores; the last one ragged) and row segments of 1, 2, 7 and 16 rows or
+    the length chosen for the device, 100 steps: segments of one and two rows run only the
+    prologue and the last-row paths."""
     c = MARCH_2D[case]()
     ref = oracle_fields(("2d-march", case), c, 100)
     assert_parity(gpu_fields(E, c, 100, store, 0, tz=tz), ref, TOL[store], (case, store, tz))
