@@ -127,7 +127,7 @@ MARCH_2D = {
 @pytest.mark.parametrize("tz", [1, 2, 7, 16, None])
 @pytest.mark.parametrize("case,store", [("periodic", "f64"), ("periodic", "f32"), ("periodic", "f16dev"),
                                         ("zerograd", "f64"), ("zerograd", "f32"), ("zerograd", "f16dev"),
-                                        ("periodic-zm", "f64")])
+                                        ("periodic", "bf16dev"), ("periodic-zm", "f64")])
 def test_d2q9_row_march_segments(E, case, store, tz):
     """The D2Q9 row march over grids of several strips (128 nodes for FP64 and FP32, 256
     for the 16-bit stores; the last one ragged) and row segments of 1, 2, 7 and 16 rows or
